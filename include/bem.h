@@ -1,0 +1,197 @@
+/*
+ * bem.h -- C ABI of the GB300 panel-interaction library (libbem.so).
+ *
+ * The library evaluates the indirect single-layer boundary element method of
+ * "Dielectric Breakdown Prediction with GPU-Accelerated BEM" (arXiv:2003.12663):
+ * a virtual surface charge sigma, piecewise constant on flat triangles
+ * (Sec. 3), generates the potential
+ *
+ *     phi(x) = sum_j u_j S_j(x),   S_j(x) = 1/(4 pi) int_{tau_j} 1/|x-y| dS_y        (Eq. SL)
+ *
+ * and the field
+ *
+ *     E(x)   = sum_j u_j G_j(x),   G_j(x) = 1/(4 pi) int_{tau_j} (x-y)/|x-y|^3 dS_y
+ *
+ * (field formula at the end of Sec. 2).  A pair (x, tau_j) is regular when the
+ * distance D from x to the circumcentre of tau_j exceeds eta * R_j, R_j the
+ * circumradius (Sec. 4); regular pairs are integrated by a Duffy-transformed
+ * Gauss rule with g x g nodes, all other pairs by the closed-form integral of a
+ * uniform density over a flat triangle, in FP64.
+ *
+ * Units: potentials and fields are those of phi = int sigma/(4 pi r); the
+ * permittivities are relative values.  Unit normals point out of every body,
+ * toward eps_plus; a triangle's vertices are counter-clockwise about its normal.
+ *
+ * Conventions for every call:
+ *  - the return value is a status (BEM_OK or a negative BEM_ERR_*); no call
+ *    throws, aborts or exits; bem_last_error() gives a message for the last error;
+ *  - "dev" pointers are CUDA device pointers, "host" pointers host memory; all of
+ *    them are owned by the caller and are only read or written during the call
+ *    (device work is queued on the context's stream and may still be running when
+ *    the call returns, except where a call says it synchronises);
+ *  - arrays are dense, row-major, in the element type stated;
+ *  - a context owns only the precomputed panel data and a fixed workspace sized
+ *    at bem_create; the evaluation calls allocate no device memory;
+ *  - one context is used by one host thread at a time.
+ */
+#ifndef BEM_H
+#define BEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BEM_OK = 0,
+    BEM_ERR_ARG = -1,           /* an argument is out of range or a pointer is NULL */
+    BEM_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+    BEM_ERR_DEGENERATE = -3,    /* a triangle has zero area */
+    BEM_ERR_NOT_CONVERGED = -4, /* the solver stopped at its iteration limit */
+    BEM_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up */
+    BEM_ERR_NOMEM = -6,         /* a device allocation in bem_create failed */
+    BEM_ERR_CAPACITY = -7       /* a size exceeds the workspace fixed at bem_create */
+};
+
+/* Boundary condition of a group of triangles (Sec. 2, Eqs. Final1-Final4). */
+enum { BEM_CONDUCTOR = 0, BEM_FLOATING = 1, BEM_DIELECTRIC = 2 };
+
+/* Arithmetic of the regular (far-field) pairs.  BEM_FP64: every step in FP64.
+ * BEM_MIXED: regular pairs in FP32 with compensated FP32 accumulation; the
+ * closed-form near pairs, reductions and everything else in FP64. */
+enum { BEM_FP64 = 0, BEM_MIXED = 1 };
+
+typedef struct {
+    int32_t kind;        /* BEM_CONDUCTOR, BEM_FLOATING or BEM_DIELECTRIC */
+    int32_t floating_id; /* BEM_FLOATING: 0 .. n_floating-1, one id per floating body */
+    double V0;           /* BEM_CONDUCTOR: prescribed potential (Eq. conductor) */
+    double eps_plus;     /* permittivity on the normal's side (Eqs. Jump, Final4, Final3) */
+    double eps_minus;    /* BEM_DIELECTRIC: permittivity on the other side */
+} bem_region;
+
+typedef struct {
+    int64_t nv;                 /* number of vertices */
+    int64_t np;                 /* number of triangles N */
+    const double* X;            /* host [nv][3] vertex coordinates */
+    const int32_t* tri;         /* host [np][3] vertex indices, CCW about the outward normal */
+    const int32_t* region;      /* host [np] index into regions */
+    int32_t nregions;
+    const bem_region* regions;  /* host [nregions] */
+} bem_mesh;
+
+typedef struct {
+    double eta;              /* pair is regular iff D > eta R (Sec. 4); default 4 */
+    int32_t far_order;       /* g: Duffy/Gauss rule with g x g nodes; 1..6, default 3 */
+    int32_t gmres_restart;   /* restart length m of GMRES(m); default 100 */
+    int32_t max_iters;       /* total GMRES iteration limit per solve; default 2000 */
+    int32_t max_refine;      /* BEM_MIXED: iterative-refinement steps; default 6 */
+    int64_t max_points;      /* largest M of one bem_eval_field chunk; default 131072 */
+    int32_t near_cap;        /* most near pairs one evaluation point may have; default 1024 */
+    int32_t reserved;
+} bem_params;
+
+typedef struct bem_ctx bem_ctx;
+
+/* Fill p with the defaults above.  Never fails. */
+void bem_default_params(bem_params* p);
+
+/*
+ * Create a context for one mesh: copies the mesh to the device of the current
+ * CUDA device, computes per-triangle geometry and quadrature nodes, the near
+ * pairs of every collocation point (centroid) with their closed-form values, and
+ * allocates the workspace.  stream: cudaStream_t (NULL = legacy default stream)
+ * on which every later call of this context queues its work.  params may be NULL
+ * (defaults).  Synchronises the stream before returning.
+ * Errors: BEM_ERR_ARG (bad sizes, indices, region data), BEM_ERR_DEGENERATE,
+ * BEM_ERR_NOMEM, BEM_ERR_CUDA.  On error *out is NULL.
+ */
+int bem_create(bem_ctx** out, const bem_mesh* mesh, const bem_params* params, void* stream);
+
+/* Free a context (NULL is allowed).  Synchronises its stream first. */
+int bem_destroy(bem_ctx* ctx);
+
+/* Message of the last error on ctx, or of the last failed bem_create if ctx is NULL. */
+const char* bem_last_error(const bem_ctx* ctx);
+
+/* Sizes: N triangles, N + n_floating unknowns, n_floating, near pairs of the
+ * collocation points (any output pointer may be NULL). */
+int bem_sizes(const bem_ctx* ctx, int64_t* n_panels, int64_t* n_unknowns, int64_t* n_floating,
+              int64_t* near_pairs);
+
+/* Wait for the context's stream; returns BEM_ERR_TIMEOUT if a device-side wait
+ * gave up since the last call, else BEM_OK or BEM_ERR_CUDA. */
+int bem_sync(bem_ctx* ctx);
+
+/*
+ * Rows [row0, row1) of the dense collocation matrix A of Eqs. Final1-Final4
+ * (Sec. 3: sigma_h = sum_j u_j psi_j, psi_j = 1 on tau_j; equations imposed at
+ * the centroids c_i).  The unknowns are u_0..u_{N-1} followed by the potentials
+ * V_f of the floating bodies; A is (N+F) x (N+F).  Row i < N with normal n_i:
+ *   conductor : A_ij = S_j(c_i)
+ *   floating f: A_ij = S_j(c_i),                      A_{i,N+f} = -1
+ *   dielectric: A_ij = (eps+ - eps-) n_i.G_j(c_i) + delta_ij (eps+ + eps-)/2
+ * Row N+f (charge neutrality of floating body f, Eq. Final4 by the centroid rule,
+ * divided by the body's area):  A_{N+f,j} = sum_{i in f} A_i eps+ (delta_ij/2 + n_i.G_j(c_i)) / area_f.
+ * n_i.G_i(c_i) is the principal value, 0 for a flat triangle.
+ * A_dev: device, row-major double, (row1-row0) rows of leading dimension lda >= N+F.
+ * precision: BEM_FP64 or BEM_MIXED (regular pairs rounded to FP32).
+ */
+int bem_assemble_rows(bem_ctx* ctx, int64_t row0, int64_t row1, int32_t precision, double* A_dev,
+                      int64_t lda);
+
+/*
+ * y = A x without forming A (matrix-free): far pairs by the quadrature kernel,
+ * near pairs from the precomputed closed-form values, then the row equations
+ * above.  x_dev, y_dev: device double [nrhs][N+F].  1 <= nrhs <= 4.
+ */
+int bem_matvec(bem_ctx* ctx, int32_t precision, int32_t nrhs, const double* x_dev, double* y_dev);
+
+/*
+ * Right-hand side b of Eqs. Final1-Final4: b_i = V0 of row i's conductor, 0 on
+ * every other row.  V0_dev: device double [nrhs][nregions] of conductor
+ * potentials (entries of other regions ignored), or NULL for the mesh's V0.
+ * b_dev: device double [nrhs][N+F].
+ */
+int bem_rhs(bem_ctx* ctx, int32_t nrhs, const double* V0_dev, double* b_dev);
+
+/*
+ * Solve A u = b (b from bem_rhs with V0_dev) by restarted GMRES with right
+ * Jacobi scaling (Sec. 3; Sec. 5 names GMRES with a diagonal preconditioner) to
+ * ||b - A u|| <= tol ||b|| (unpreconditioned 2-norm).  BEM_FP64: every matvec in
+ * FP64.  BEM_MIXED: GMRES on the mixed matvec inside an iterative refinement
+ * whose residual b - A u is formed with the FP64 matvec.  u_dev: device double
+ * [nrhs][N+F]; its input value is ignored (start from 0).  iters (host, may be
+ * NULL): total GMRES iterations; relres (host, may be NULL): final FP64 relative
+ * residual per right-hand side, [nrhs].  Synchronises the stream (it reads the
+ * Krylov coefficients back).  BEM_ERR_NOT_CONVERGED if tol was not reached within
+ * max_iters (u then holds the last iterate).
+ */
+int bem_solve(bem_ctx* ctx, int32_t precision, int32_t nrhs, const double* V0_dev, double* u_dev,
+              double tol, int32_t* iters, double* relres);
+
+/*
+ * phi and E at M arbitrary points (field formula of Sec. 2):
+ *   phi(x) = sum_j u_j S_j(x),  E(x) = sum_j u_j G_j(x).
+ * Points closer than eta R_j to a triangle's circumcentre take its closed form in
+ * FP64.  A point lying exactly on a triangle gets the principal value of that
+ * triangle's normal field.  u_dev: device double [>= N] (entries >= N ignored);
+ * pts_dev: device double [M][3]; phi_dev: device double [M] or NULL; E_dev:
+ * device double [M][3] or NULL.  Any M >= 0 (processed in chunks of max_points).
+ * BEM_ERR_CAPACITY if a point has more than near_cap near triangles.
+ */
+int bem_eval_field(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t M,
+                   const double* pts_dev, double* phi_dev, double* E_dev);
+
+/*
+ * Field on the + side of the surface at every centroid ("E surface" of Sec. 5):
+ *   E+(c_i) = E_PV(c_i) + u_i n_i / 2   (Eq. ADL read as E+.n = sigma/2 + K' sigma).
+ * E_dev: device double [N][3].
+ */
+int bem_surface_field(bem_ctx* ctx, int32_t precision, const double* u_dev, double* E_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_H */

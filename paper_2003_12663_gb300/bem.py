@@ -1,0 +1,219 @@
+"""Thin Python binding of libbem.so (include/bem.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch only provides device
+memory and the stream.  There is no CPU fallback: if the library is missing or
+fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbem.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "bem.h")
+
+FP64, MIXED = 0, 1
+CONDUCTOR, FLOATING, DIELECTRIC = 0, 1, 2
+_KIND = {"conductor": CONDUCTOR, "floating": FLOATING, "dielectric": DIELECTRIC}
+
+ERRORS = {0: "BEM_OK", -1: "BEM_ERR_ARG", -2: "BEM_ERR_CUDA", -3: "BEM_ERR_DEGENERATE",
+          -4: "BEM_ERR_NOT_CONVERGED", -5: "BEM_ERR_TIMEOUT", -6: "BEM_ERR_NOMEM",
+          -7: "BEM_ERR_CAPACITY"}
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class bem_region(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("floating_id", ctypes.c_int32), ("V0", ctypes.c_double),
+                ("eps_plus", ctypes.c_double), ("eps_minus", ctypes.c_double)]
+
+
+class bem_mesh(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("np", ctypes.c_int64),
+                ("X", ctypes.POINTER(ctypes.c_double)), ("tri", ctypes.POINTER(ctypes.c_int32)),
+                ("region", ctypes.POINTER(ctypes.c_int32)), ("nregions", ctypes.c_int32),
+                ("regions", ctypes.POINTER(bem_region))]
+
+
+class bem_params(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("far_order", ctypes.c_int32),
+                ("gmres_restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("max_points", ctypes.c_int64),
+                ("near_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_i32, _i64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "bem_default_params": (None, [ctypes.POINTER(bem_params)]),
+    "bem_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(bem_mesh), ctypes.POINTER(bem_params), _vp]),
+    "bem_destroy": (_i32, [_vp]),
+    "bem_last_error": (ctypes.c_char_p, [_vp]),
+    "bem_sizes": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                         ctypes.POINTER(_i64)]),
+    "bem_sync": (_i32, [_vp]),
+    "bem_assemble_rows": (_i32, [_vp, _i64, _i64, _i32, _vp, _i64]),
+    "bem_matvec": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+    "bem_rhs": (_i32, [_vp, _i32, _vp, _vp]),
+    "bem_solve": (_i32, [_vp, _i32, _i32, _vp, _vp, _dbl, ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
+    "bem_eval_field": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp]),
+    "bem_surface_field": (_i32, [_vp, _i32, _vp, _vp]),
+}
+_lib = None
+
+
+def header_symbols(path: str = HEADER):
+    """Names of the functions declared in include/bem.h."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bem_[a-z_0-9]+)\s*\(", txt)))
+
+
+def lib():
+    """Load libbem.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libbem.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        msg = lib().bem_last_error(ctx)
+        raise BemError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def default_params(**kw) -> bem_params:
+    p = bem_params()
+    lib().bem_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One mesh on the current CUDA device (bem_create / bem_destroy)."""
+
+    def __init__(self, mesh, stream=None, **params):
+        import torch
+        self._torch = torch
+        L = lib()
+        self.X = np.ascontiguousarray(mesh.X, dtype=np.float64)
+        self.tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
+        self.region = np.ascontiguousarray(mesh.region, dtype=np.int32)
+        regs = (bem_region * len(mesh.regions))()
+        for k, r in enumerate(mesh.regions):
+            regs[k].kind = _KIND[r["kind"]]
+            regs[k].floating_id = int(r.get("floating_id", 0))
+            regs[k].V0 = float(r.get("V0", 0.0))
+            regs[k].eps_plus = float(r.get("eps_plus", 1.0))
+            regs[k].eps_minus = float(r.get("eps_minus", 1.0))
+        self._regs = regs
+        m = bem_mesh(len(self.X), len(self.tri), self.X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     self.tri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                     self.region.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(mesh.regions),
+                     regs)
+        self.params = default_params(**params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = L.bem_create(ctypes.byref(h), ctypes.byref(m), ctypes.byref(self.params),
+                          ctypes.c_void_p(self.stream.cuda_stream))
+        _check(rc, None)
+        self.h = h
+        a, b, c, d = (ctypes.c_int64() for _ in range(4))
+        _check(L.bem_sizes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), h)
+        self.np, self.nunk, self.nfloat, self.near_pairs = a.value, b.value, c.value, d.value
+        self.nregions = len(mesh.regions)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a, dtype=None):
+        t = self._torch
+        x = a if isinstance(a, t.Tensor) else t.as_tensor(np.asarray(a))
+        return x.to(device="cuda", dtype=dtype or t.float64).contiguous()
+
+    def sync(self):
+        _check(lib().bem_sync(self.h), self.h)
+
+    def rhs(self, V0=None, nrhs=1):
+        t = self._torch
+        b = t.empty((nrhs, self.nunk), dtype=t.float64, device="cuda")
+        v = None if V0 is None else self._dev(V0)
+        _check(lib().bem_rhs(self.h, nrhs, _ptr(v), _ptr(b)), self.h)
+        return b
+
+    def matvec(self, x, precision=FP64, out=None):
+        t = self._torch
+        x = self._dev(x)
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        y = out if out is not None else t.empty_like(x)
+        _check(lib().bem_matvec(self.h, precision, nrhs, _ptr(x), _ptr(y)), self.h)
+        return y
+
+    def solve(self, precision=FP64, V0=None, tol=1e-8, nrhs=1, out=None):
+        t = self._torch
+        v = None if V0 is None else self._dev(V0)
+        u = out if out is not None else t.empty((nrhs, self.nunk), dtype=t.float64, device="cuda")
+        it = ctypes.c_int32()
+        rel = (ctypes.c_double * nrhs)()
+        rc = lib().bem_solve(self.h, precision, nrhs, _ptr(v), _ptr(u), tol, ctypes.byref(it), rel)
+        _check(rc, self.h)
+        return u, it.value, list(rel)
+
+    def eval_field(self, u, pts, precision=FP64, want_phi=True, want_E=True, phi=None, E=None):
+        t = self._torch
+        u = self._dev(u)
+        pts = self._dev(pts)
+        M = pts.shape[0]
+        if want_phi and phi is None:
+            phi = t.empty(M, dtype=t.float64, device="cuda")
+        if want_E and E is None:
+            E = t.empty((M, 3), dtype=t.float64, device="cuda")
+        _check(lib().bem_eval_field(self.h, precision, _ptr(u), M, _ptr(pts),
+                                    _ptr(phi if want_phi else None), _ptr(E if want_E else None)),
+               self.h)
+        return phi, E
+
+    def surface_field(self, u, precision=FP64):
+        t = self._torch
+        u = self._dev(u)
+        E = t.empty((self.np, 3), dtype=t.float64, device="cuda")
+        _check(lib().bem_surface_field(self.h, precision, _ptr(u), _ptr(E)), self.h)
+        return E
+
+    def assemble_rows(self, row0=0, row1=None, precision=FP64):
+        t = self._torch
+        row1 = self.nunk if row1 is None else row1
+        A = t.empty((row1 - row0, self.nunk), dtype=t.float64, device="cuda")
+        _check(lib().bem_assemble_rows(self.h, row0, row1, precision, _ptr(A), self.nunk), self.h)
+        return A

@@ -1,0 +1,206 @@
+// bem_internal.cuh -- context layout, device helpers and launchers shared by the
+// translation units of libbem.so.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bem.h"
+
+// ---------------------------------------------------------------- panel record
+// Per triangle, FP64, 24 doubles (192 B, 16-B aligned):
+//   a[3] b[3] c[3]  vertices (CCW about n)
+//   n[3]            unit normal
+//   area
+//   ctr[3]          centroid (collocation point, Sec. 3)
+//   cc[3]           circumcentre (classification, Sec. 4)
+//   R               circumradius
+//   etaR            eta * R
+//   pad[2]
+enum { GEO_A = 0, GEO_B = 3, GEO_C = 6, GEO_N = 9, GEO_AREA = 12, GEO_CTR = 13, GEO_CC = 16,
+       GEO_R = 19, GEO_ETAR = 20, GEO_STRIDE = 24 };
+
+constexpr int kMaxOrder = 6;          // largest far_order g
+constexpr int kMaxRhs = 4;            // right-hand sides per matvec launch
+constexpr double kInv4Pi = 0.07957747154594767;  // 1/(4 pi)
+
+struct bem_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    bem_params prm{};
+    int64_t nv = 0, np = 0, nunk = 0;
+    int nfloat = 0;
+    int g = 3, Q = 9;
+    std::vector<bem_region> regions;
+    std::vector<int32_t> h_region;
+    std::vector<double> h_rule_u, h_rule_wu, h_rule_v, h_rule_wv;  // the far rule, host copy
+
+    // geometry
+    double* X = nullptr;        // [nv][3]
+    int32_t* tri = nullptr;     // [np][3]
+    double* geo = nullptr;      // [np][GEO_STRIDE]
+    float4* hdr32 = nullptr;    // [np] (cc, (eta R)^2)    FP32
+    double4* hdr64 = nullptr;   // [np] (cc, (eta R)^2)    FP64
+    float4* node32 = nullptr;   // [np][Q] (y, w)          FP32
+    double4* node64 = nullptr;  // [np][Q] (y, w)          FP64
+    float4* tgt32 = nullptr;    // [np] centroids          FP32
+    double4* tgt64 = nullptr;   // [np] centroids          FP64
+
+    // rows (Eqs. Final1-Final4)
+    int32_t* row_kind = nullptr;   // [np]
+    int32_t* row_aux = nullptr;    // [np] floating id or region index of a conductor
+    double* row_a = nullptr;       // [np] dielectric: (eps+ + eps-)/2
+    double* row_b = nullptr;       // [np] dielectric: eps+ - eps-
+    double* row_w = nullptr;       // [np] floating: A_i eps+ / area_f
+    double* region_V0 = nullptr;   // [nregions]
+    int32_t* float_rows = nullptr; // rows of every floating body, grouped
+    int32_t* float_off = nullptr;  // [nfloat+1]
+    double* jinv = nullptr;        // [nunk] inverse Jacobi diagonal
+
+    // near pairs of the collocation points (CSR over rows, columns ascending)
+    int64_t nnz = 0;
+    int64_t* near_ptr = nullptr;   // [np+1]
+    int32_t* near_col = nullptr;   // [nnz]
+    double4* near_val = nullptr;   // [nnz] exact (S, G) of the pair, G's normal part PV for i==j
+    uint8_t* near_flag = nullptr;  // [nnz] bit0: near in FP32 classification, bit1: in FP64
+
+    // workspace
+    double* part = nullptr;        // far partial sums
+    size_t part_cap = 0;           // doubles
+    double* field = nullptr;       // [kMaxRhs][np][4] reduced phi, E at the centroids
+    double* neut = nullptr;        // [kMaxRhs][np] neutrality contributions
+    double* pts_stage = nullptr;   // staging for host points (unused by device-pointer calls)
+
+    // solver workspace
+    int m = 100;
+    double* V = nullptr;           // [(m+1)][nunk] Krylov basis
+    double* wvec = nullptr;        // [nunk]
+    double* zvec = nullptr;        // [nunk]
+    double* rvec = nullptr;        // [nunk]
+    double* bvec = nullptr;        // [nunk]
+    double* dvec = nullptr;        // [nunk]
+    double* ivec = nullptr;        // [nunk]
+    double* hcol = nullptr;        // [2(m+2)] device Hessenberg column scratch
+    double* hcol_host = nullptr;   // pinned mirror
+    int* d_status = nullptr;       // device-side status word
+
+    std::string err;
+};
+
+// ---------------------------------------------------------------- error helpers
+int set_err(bem_ctx* ctx, int code, const char* fmt, ...);
+#define BEM_CUDA_TRY(ctx, call)                                                              \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return set_err((ctx), BEM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+#define BEM_LAUNCH_CHECK(ctx) BEM_CUDA_TRY(ctx, cudaGetLastError())
+
+// ---------------------------------------------------------------- device helpers
+// The pair classification of Sec. 4, written once per precision with explicit
+// rounding so that every kernel of that precision takes the same decision for
+// the same (target, triangle): regular ("far") iff |x - cc|^2 > (eta R)^2.
+__device__ __forceinline__ bool is_far32(float x, float y, float z, float4 h)
+{
+    const float dx = __fsub_rn(x, h.x), dy = __fsub_rn(y, h.y), dz = __fsub_rn(z, h.z);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    return d2 > h.w;
+}
+
+__device__ __forceinline__ bool is_far64(double x, double y, double z, double4 h)
+{
+    const double dx = __dsub_rn(x, h.x), dy = __dsub_rn(y, h.y), dz = __dsub_rn(z, h.z);
+    const double d2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+    return d2 > h.w;
+}
+
+// Closed-form integrals of a uniform unit density over a flat triangle (FP64).
+// For every edge p->q (unit tangent t, outward in-plane normal m = t x n) the
+// line integral f = int_edge dl/|x-y| is taken in the form that avoids
+// cancellation: with s0 = (p-x).t, s1 = (q-x).t, r0 = |p-x|, r1 = |q-x|,
+// L = |q-p|,
+//   s0 >= 0: f = log1p(L (s0+s1+r0+r1) / ((r0+r1)(r0+s0)))
+//   s1 <= 0: f = log1p(L (r0+r1-s0-s1) / ((r0+r1)(r1-s1)))
+//   else   : f = log((r1+s1)(r0-s0) / (d^2+h^2)),  d = (p-x).m, h = (x-a).n.
+// With the signed solid angle Omega of the triangle seen from x (Van Oosterom &
+// Strackee; negative on the side n points to):
+//   4 pi S = sum d f + h Omega,   4 pi G = sum m f - Omega n.
+// own != 0: x is this triangle's centroid, the normal part of G is its
+// principal value (0) and h = 0.
+__device__ __forceinline__ void tri_closed_form(const double* __restrict__ gp, double x,
+                                                double y, double z, bool own, double& S,
+                                                double& Gx, double& Gy, double& Gz)
+{
+    const double nx = gp[GEO_N], ny = gp[GEO_N + 1], nz = gp[GEO_N + 2];
+    const double h = own ? 0.0 : (x - gp[GEO_A]) * nx + (y - gp[GEO_A + 1]) * ny + (z - gp[GEO_A + 2]) * nz;
+    double sdf = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    double ax[3], ay[3], az[3], al[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ax[i] = gp[3 * i] - x;
+        ay[i] = gp[3 * i + 1] - y;
+        az[i] = gp[3 * i + 2] - z;
+        al[i] = sqrt(ax[i] * ax[i] + ay[i] * ay[i] + az[i] * az[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int k = (i + 1) % 3;
+        const double ex = ax[k] - ax[i], ey = ay[k] - ay[i], ez = az[k] - az[i];
+        const double L = sqrt(ex * ex + ey * ey + ez * ez);
+        const double tx = ex / L, ty = ey / L, tz = ez / L;
+        const double mx = ty * nz - tz * ny, my = tz * nx - tx * nz, mz = tx * ny - ty * nx;
+        const double s0 = ax[i] * tx + ay[i] * ty + az[i] * tz;
+        const double s1 = ax[k] * tx + ay[k] * ty + az[k] * tz;
+        const double r0 = al[i], r1 = al[k];
+        const double d = ax[i] * mx + ay[i] * my + az[i] * mz;
+        double f;
+        if (s0 >= 0.0)
+            f = log1p(L * (s0 + s1 + r0 + r1) / ((r0 + r1) * (r0 + s0)));
+        else if (s1 <= 0.0)
+            f = log1p(L * (r0 + r1 - s0 - s1) / ((r0 + r1) * (r1 - s1)));
+        else
+            f = log((r1 + s1) * (r0 - s0) / (d * d + h * h));
+        if (d != 0.0) sdf += d * f;
+        fx += mx * f;
+        fy += my * f;
+        fz += mz * f;
+    }
+    double om = 0.0;
+    if (!own) {
+        const double det = ax[0] * (ay[1] * az[2] - az[1] * ay[2]) - ay[0] * (ax[1] * az[2] - az[1] * ax[2]) +
+                           az[0] * (ax[1] * ay[2] - ay[1] * ax[2]);
+        const double d01 = ax[0] * ax[1] + ay[0] * ay[1] + az[0] * az[1];
+        const double d02 = ax[0] * ax[2] + ay[0] * ay[2] + az[0] * az[2];
+        const double d12 = ax[1] * ax[2] + ay[1] * ay[2] + az[1] * az[2];
+        const double den = al[0] * al[1] * al[2] + d01 * al[2] + d02 * al[1] + d12 * al[0];
+        om = 2.0 * atan2(det, den);
+    }
+    S = kInv4Pi * (sdf + h * om);
+    Gx = kInv4Pi * (fx - om * nx);
+    Gy = kInv4Pi * (fy - om * ny);
+    Gz = kInv4Pi * (fz - om * nz);
+}
+
+// ---------------------------------------------------------------- launchers
+// far.cu: partial sums of sum_j u_j (S_j, G_j)(x_t) over regular pairs, one
+// (split, target) record of 4 doubles per right-hand side.
+struct FarTargets {
+    const float4* t32;       // FP32 targets (x,y,z,-) or nullptr
+    const double4* t64;      // FP64 targets (x,y,z,-) or nullptr
+    const double* tpts;      // or raw double [M][3]
+    int64_t M;
+};
+int far_splits(const bem_ctx* ctx, int precision, int64_t M);
+int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, int nrhs,
+               int64_t ustride, int splits, double* part);
+
+// field.cu
+int matvec_impl(bem_ctx* ctx, int precision, int nrhs, const double* x, double* y);
+
+// setup.cu
+void host_gauss_rule(int n, int weight_power, std::vector<double>& x, std::vector<double>& w);

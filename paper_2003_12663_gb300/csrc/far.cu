@@ -1,0 +1,288 @@
+// far.cu -- the regular-pair interaction kernels (Sec. 4, regular pairs by the
+// Duffy/Gauss rule).  For every target x_t and every triangle j whose pair with
+// x_t is regular (D > eta R), accumulate
+//     phi_t += u_j sum_k w_jk / |x_t - y_jk|
+//     E_t   += u_j sum_k w_jk (x_t - y_jk) / |x_t - y_jk|^3
+// (times 1/(4 pi), applied by the consumers).  Near pairs are skipped here and
+// handled in FP64 by the closed form afterwards (the deferred second pass of
+// Sec. 4 / Fig. 3).
+//
+// Layout: one CTA owns a tile of kThreads*TR targets (TR per thread, register
+// blocked) and one contiguous slice ("split") of triangles.  Triangles are
+// staged through shared memory in chunks of PC: the classification header
+// (circumcentre, (eta R)^2), the density u_j and the Q quadrature nodes (y, w),
+// each node read by every thread of the CTA for all of its TR targets.  The CTA
+// writes one partial (phi, E) per target and split; the consumer adds the
+// splits in FP64.
+//
+// FP32 form: per triangle the Q node contributions are summed in FP32, folded
+// into a per-chunk FP32 partial with u_j (masked to 0 for near pairs), and the
+// chunk partials are added with Kahan compensation.
+#include "bem_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kTR32 = 4;
+constexpr int kTR64 = 2;
+constexpr int kPC32 = 32;
+constexpr int kPC64 = 16;
+
+template <int TR, int Q, bool RAW>
+__global__ void __launch_bounds__(kThreads)
+k_far32(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_t M,
+        const float4* __restrict__ hdr, const float4* __restrict__ node,
+        const double* __restrict__ u, int64_t np, int64_t per_split, double* __restrict__ part)
+{
+    constexpr int PC = kPC32;
+    __shared__ float4 s_hdr[PC];
+    __shared__ float s_u[PC];
+    __shared__ float4 s_node[PC * Q];
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * TR);
+    const int split = blockIdx.y;
+    const int64_t p0 = (int64_t)split * per_split;
+    const int64_t p1 = min(np, p0 + per_split);
+
+    float tx[TR], ty[TR], tz[TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int64_t t = min(base + r * kThreads + tid, M - 1);
+        if (RAW) {
+            tx[r] = __double2float_rn(tpts[3 * t]);
+            ty[r] = __double2float_rn(tpts[3 * t + 1]);
+            tz[r] = __double2float_rn(tpts[3 * t + 2]);
+        } else {
+            const float4 v = t32[t];
+            tx[r] = v.x; ty[r] = v.y; tz[r] = v.z;
+        }
+    }
+    float acc[TR][4], cmp[TR][4];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = cmp[r][c] = 0.f;
+
+    for (int64_t c0 = p0; c0 < p1; c0 += PC) {
+        const int npc = (int)min((int64_t)PC, p1 - c0);
+        __syncthreads();
+        for (int k = tid; k < npc; k += kThreads) {
+            s_hdr[k] = hdr[c0 + k];
+            s_u[k] = __double2float_rn(u[c0 + k]);
+        }
+        for (int k = tid; k < npc * Q; k += kThreads) s_node[k] = node[c0 * Q + k];
+        __syncthreads();
+        float cp[TR][4];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cp[r][c] = 0.f;
+        for (int p = 0; p < npc; ++p) {
+            float ps[TR], gx[TR], gy[TR], gz[TR];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const float4 nd = s_node[p * Q + k];
+#pragma unroll
+                for (int r = 0; r < TR; ++r) {
+                    const float dx = tx[r] - nd.x, dy = ty[r] - nd.y, dz = tz[r] - nd.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f)));
+                    const float ri = rsqrtf(r2);
+                    const float t = nd.w * ri;
+                    const float t3 = t * (ri * ri);
+                    if (k == 0) {
+                        ps[r] = t;
+                        gx[r] = t3 * dx; gy[r] = t3 * dy; gz[r] = t3 * dz;
+                    } else {
+                        ps[r] += t;
+                        gx[r] = fmaf(t3, dx, gx[r]);
+                        gy[r] = fmaf(t3, dy, gy[r]);
+                        gz[r] = fmaf(t3, dz, gz[r]);
+                    }
+                }
+            }
+            const float4 h = s_hdr[p];
+            const float up = s_u[p];
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const float m = is_far32(tx[r], ty[r], tz[r], h) ? up : 0.f;
+                cp[r][0] = fmaf(m, ps[r], cp[r][0]);
+                cp[r][1] = fmaf(m, gx[r], cp[r][1]);
+                cp[r][2] = fmaf(m, gy[r], cp[r][2]);
+                cp[r][3] = fmaf(m, gz[r], cp[r][3]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {  // Kahan: acc + cmp carries the exact running sum
+                const float y = cp[r][c] - cmp[r][c];
+                const float t = acc[r][c] + y;
+                cmp[r][c] = (t - acc[r][c]) - y;
+                acc[r][c] = t;
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int64_t t = base + r * kThreads + tid;
+        if (t < M) {
+            double* o = part + ((int64_t)split * M + t) * 4;
+            o[0] = (double)acc[r][0] - (double)cmp[r][0];
+            o[1] = (double)acc[r][1] - (double)cmp[r][1];
+            o[2] = (double)acc[r][2] - (double)cmp[r][2];
+            o[3] = (double)acc[r][3] - (double)cmp[r][3];
+        }
+    }
+}
+
+template <int TR, int Q, bool RAW>
+__global__ void __launch_bounds__(kThreads)
+k_far64(const double4* __restrict__ t64, const double* __restrict__ tpts, int64_t M,
+        const double4* __restrict__ hdr, const double4* __restrict__ node,
+        const double* __restrict__ u, int64_t np, int64_t per_split, double* __restrict__ part)
+{
+    constexpr int PC = kPC64;
+    __shared__ double4 s_hdr[PC];
+    __shared__ double s_u[PC];
+    __shared__ double4 s_node[PC * Q];
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * TR);
+    const int split = blockIdx.y;
+    const int64_t p0 = (int64_t)split * per_split;
+    const int64_t p1 = min(np, p0 + per_split);
+
+    double tx[TR], ty[TR], tz[TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int64_t t = min(base + r * kThreads + tid, M - 1);
+        if (RAW) {
+            tx[r] = tpts[3 * t]; ty[r] = tpts[3 * t + 1]; tz[r] = tpts[3 * t + 2];
+        } else {
+            const double4 v = t64[t];
+            tx[r] = v.x; ty[r] = v.y; tz[r] = v.z;
+        }
+    }
+    double acc[TR][4];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+
+    for (int64_t c0 = p0; c0 < p1; c0 += PC) {
+        const int npc = (int)min((int64_t)PC, p1 - c0);
+        __syncthreads();
+        for (int k = tid; k < npc; k += kThreads) {
+            s_hdr[k] = hdr[c0 + k];
+            s_u[k] = u[c0 + k];
+        }
+        for (int k = tid; k < npc * Q; k += kThreads) s_node[k] = node[c0 * Q + k];
+        __syncthreads();
+        for (int p = 0; p < npc; ++p) {
+            double ps[TR], gx[TR], gy[TR], gz[TR];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const double4 nd = s_node[p * Q + k];
+#pragma unroll
+                for (int r = 0; r < TR; ++r) {
+                    const double dx = tx[r] - nd.x, dy = ty[r] - nd.y, dz = tz[r] - nd.z;
+                    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, 1e-200)));
+                    const double ri = rsqrt(r2);
+                    const double t = nd.w * ri;
+                    const double t3 = t * (ri * ri);
+                    if (k == 0) {
+                        ps[r] = t;
+                        gx[r] = t3 * dx; gy[r] = t3 * dy; gz[r] = t3 * dz;
+                    } else {
+                        ps[r] += t;
+                        gx[r] = fma(t3, dx, gx[r]);
+                        gy[r] = fma(t3, dy, gy[r]);
+                        gz[r] = fma(t3, dz, gz[r]);
+                    }
+                }
+            }
+            const double4 h = s_hdr[p];
+            const double up = s_u[p];
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const double m = is_far64(tx[r], ty[r], tz[r], h) ? up : 0.0;
+                acc[r][0] = fma(m, ps[r], acc[r][0]);
+                acc[r][1] = fma(m, gx[r], acc[r][1]);
+                acc[r][2] = fma(m, gy[r], acc[r][2]);
+                acc[r][3] = fma(m, gz[r], acc[r][3]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int64_t t = base + r * kThreads + tid;
+        if (t < M) {
+            double* o = part + ((int64_t)split * M + t) * 4;
+            o[0] = acc[r][0]; o[1] = acc[r][1]; o[2] = acc[r][2]; o[3] = acc[r][3];
+        }
+    }
+}
+
+template <int Q>
+int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, int splits,
+             double* part)
+{
+    const int64_t np = ctx->np;
+    const int64_t per_split = (np + splits - 1) / splits;
+    const bool raw = (T.tpts != nullptr);
+    if (precision == BEM_MIXED) {
+        dim3 grid((unsigned)((T.M + kThreads * kTR32 - 1) / (kThreads * kTR32)), (unsigned)splits);
+        if (raw)
+            k_far32<kTR32, Q, true><<<grid, kThreads, 0, ctx->stream>>>(
+                nullptr, T.tpts, T.M, ctx->hdr32, ctx->node32, u, np, per_split, part);
+        else
+            k_far32<kTR32, Q, false><<<grid, kThreads, 0, ctx->stream>>>(
+                T.t32, nullptr, T.M, ctx->hdr32, ctx->node32, u, np, per_split, part);
+    } else {
+        dim3 grid((unsigned)((T.M + kThreads * kTR64 - 1) / (kThreads * kTR64)), (unsigned)splits);
+        if (raw)
+            k_far64<kTR64, Q, true><<<grid, kThreads, 0, ctx->stream>>>(
+                nullptr, T.tpts, T.M, ctx->hdr64, ctx->node64, u, np, per_split, part);
+        else
+            k_far64<kTR64, Q, false><<<grid, kThreads, 0, ctx->stream>>>(
+                T.t64, nullptr, T.M, ctx->hdr64, ctx->node64, u, np, per_split, part);
+    }
+    BEM_LAUNCH_CHECK(ctx);
+    return BEM_OK;
+}
+
+}  // namespace
+
+// Number of triangle slices for M targets: enough CTAs to give every SM about
+// four, but no slice shorter than two staging chunks.
+int far_splits(const bem_ctx* ctx, int precision, int64_t M)
+{
+    const int tr = precision == BEM_MIXED ? kTR32 : kTR64;
+    const int pc = precision == BEM_MIXED ? kPC32 : kPC64;
+    const int64_t tiles = (M + kThreads * tr - 1) / (kThreads * tr);
+    const int64_t slots = (int64_t)std::max(ctx->num_sms, 1) * 4;
+    int64_t s = tiles >= slots ? 1 : slots / std::max<int64_t>(tiles, 1);
+    s = std::min<int64_t>(s, std::max<int64_t>(1, ctx->np / (2 * pc)));
+    s = std::max<int64_t>(1, std::min<int64_t>(s, 64));
+    return (int)s;
+}
+
+int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, int nrhs,
+               int64_t ustride, int splits, double* part)
+{
+    if (T.M <= 0) return BEM_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        const double* ur = u + r * ustride;
+        double* pr = part + (size_t)r * splits * T.M * 4;
+        int rc;
+        switch (ctx->g) {
+            case 1: rc = launch_q<1>(ctx, precision, T, ur, splits, pr); break;
+            case 2: rc = launch_q<4>(ctx, precision, T, ur, splits, pr); break;
+            case 3: rc = launch_q<9>(ctx, precision, T, ur, splits, pr); break;
+            case 4: rc = launch_q<16>(ctx, precision, T, ur, splits, pr); break;
+            case 5: rc = launch_q<25>(ctx, precision, T, ur, splits, pr); break;
+            case 6: rc = launch_q<36>(ctx, precision, T, ur, splits, pr); break;
+            default: return set_err(ctx, BEM_ERR_ARG, "far_order %d not compiled", ctx->g);
+        }
+        if (rc) return rc;
+    }
+    return BEM_OK;
+}

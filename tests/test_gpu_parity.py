@@ -1,0 +1,157 @@
+"""GPU (through the C ABI) versus the FP64 CPU oracle, element by element.
+
+Tolerances:
+* FP64 form: the same steps as the oracle, so entries, matvecs and fields agree
+  to rounding (1e-11 relative to the largest entry of the row / field scale);
+  sigma after GMRES to 1e-12 within 1e-9 of the LU solution.
+* mixed form: regular pairs in FP32 (unit roundoff 6e-8 per term, compensated
+  sums), so entries and matvecs within 2e-6; sigma after FP64 iterative
+  refinement within 1e-6 (relative L2), |E| within 1e-5 of the field scale
+  max|E| (the target tolerances of the method).
+"""
+import numpy as np
+import pytest
+
+from paper_2003_12663_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bem():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2003_12663_gb300 import bem as B
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return B
+
+
+MESHES = {
+    "sphere_l3": lambda: mg.sphere_mesh(3),
+    "device_s03": lambda: mg.device_mesh(scale=0.3),
+}
+
+
+@pytest.fixture(scope="module", params=list(MESHES))
+def case(request, bem, oracle_mod):
+    mesh = MESHES[request.param]()
+    ctx = bem.Context(mesh)
+    P = oracle_mod.Problem(mesh, eta=ctx.params.eta, g=ctx.params.far_order)
+    A = P.assemble()
+    yield request.param, mesh, ctx, P, A
+    ctx.close()
+
+
+def _rel_rows(G, R):
+    scale = np.maximum(np.abs(R).max(axis=1, keepdims=True), 1e-300)
+    return np.max(np.abs(G - R) / scale)
+
+
+def test_sizes(case):
+    name, mesh, ctx, P, A = case
+    assert ctx.np == mesh.np_ and ctx.nunk == mesh.n_unknowns
+    assert ctx.near_pairs >= ctx.np  # every row holds at least its own triangle
+
+
+def test_assemble_rows_fp64(case, bem):
+    name, mesh, ctx, P, A = case
+    G = ctx.assemble_rows(precision=bem.FP64).cpu().numpy()
+    assert _rel_rows(G, A) < 1e-11
+
+
+def test_assemble_rows_mixed(case, bem):
+    name, mesh, ctx, P, A = case
+    G = ctx.assemble_rows(precision=bem.MIXED).cpu().numpy()
+    assert _rel_rows(G, A) < 2e-6
+
+
+def test_assemble_row_block(case, bem):
+    """A ragged block of rows that includes the neutrality rows, if any."""
+    name, mesh, ctx, P, A = case
+    r0, r1 = ctx.nunk - 77, ctx.nunk
+    G = ctx.assemble_rows(r0, r1, precision=bem.FP64).cpu().numpy()
+    assert _rel_rows(G, A[r0:r1]) < 1e-11
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-6)])
+def test_matvec(case, bem, prec, tol):
+    name, mesh, ctx, P, A = case
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=(3, ctx.nunk))
+    y = ctx.matvec(torch.tensor(x), precision=prec).cpu().numpy()
+    ref = x @ A.T
+    err = np.abs(y - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    assert err.max() < tol, err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_matches_lu(case, bem, prec):
+    name, mesh, ctx, P, A = case
+    u_ref = np.linalg.solve(A, P.rhs())
+    u, iters, rel = ctx.solve(prec, tol=1e-12)
+    u = u[0].cpu().numpy()
+    assert rel[0] <= 1e-12
+    err = np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)
+    assert err < (1e-9 if prec == 0 else 1e-6), (err, iters)
+    # the exact system (closed form for every pair) is within the method's budget
+    if name == "sphere_l3":
+        from oracle import oracle as O
+        u_exact = P.solve(O.EXACT)
+        assert np.linalg.norm(u - u_exact) / np.linalg.norm(u_exact) < 1e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eval_field(case, bem, prec):
+    name, mesh, ctx, P, A = case
+    u_ref = np.linalg.solve(A, P.rhs())
+    if name == "sphere_l3":
+        pts = np.concatenate([mg.sphere_eval_points(1, 1000, 1000),
+                              # near the surface: 1e-3 and 1e-6 of a panel size off the centroids
+                              P.centroids[::7] * (1 + 1e-3), P.centroids[3::11] * (1 - 1e-6)])
+    else:
+        pts = np.concatenate([mg.device_box_points(1500, 5),
+                              P.centroids[::13] + 1e-4 * P.normals[::13]])
+    pts = pts[: len(pts) - 5]  # ragged count
+    phi_r, E_r = P.field(u_ref, pts)
+    phi, E = ctx.eval_field(torch.tensor(u_ref), torch.tensor(pts), precision=prec)
+    phi, E = phi.cpu().numpy(), E.cpu().numpy()
+    tol = 1e-11 if prec == 0 else 1e-5
+    assert np.abs(phi - phi_r).max() / np.abs(phi_r).max() < tol
+    assert np.abs(E - E_r).max() / np.abs(E_r).max() < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_surface_field(case, bem, prec):
+    name, mesh, ctx, P, A = case
+    u_ref = np.linalg.solve(A, P.rhs())
+    Es_r = P.surface_field(u_ref)
+    Es = ctx.surface_field(torch.tensor(u_ref), precision=prec).cpu().numpy()
+    tol = 1e-11 if prec == 0 else 1e-5
+    assert np.abs(Es - Es_r).max() / np.abs(Es_r).max() < tol
+
+
+def test_eval_empty_and_tiny(case, bem):
+    name, mesh, ctx, P, A = case
+    u = torch.ones(ctx.nunk, dtype=torch.float64)
+    phi, E = ctx.eval_field(u, torch.zeros((0, 3), dtype=torch.float64))
+    assert phi.numel() == 0 and E.numel() == 0
+    pts = np.array([[0.05, -0.02, 7.0]])
+    phi, E = ctx.eval_field(u, torch.tensor(pts))
+    pr, Er = P.field(np.ones(ctx.nunk), pts)
+    assert abs(phi.item() - pr[0]) < 1e-12 * abs(pr[0])
+
+
+def test_rhs_and_multi_rhs(case, bem):
+    name, mesh, ctx, P, A = case
+    V0 = np.zeros((2, ctx.nregions))
+    for k, r in enumerate(mesh.regions):
+        if r["kind"] == "conductor":
+            V0[0, k], V0[1, k] = r["V0"], -2.0 * r["V0"]
+    b = ctx.rhs(torch.tensor(V0), nrhs=2).cpu().numpy()
+    assert np.allclose(b[0], P.rhs()) and np.allclose(b[1], -2.0 * P.rhs())
+    u, iters, rel = ctx.solve(0, V0=torch.tensor(V0), tol=1e-11, nrhs=2)
+    u = u.cpu().numpy()
+    assert np.allclose(u[1], -2.0 * u[0], rtol=1e-8, atol=1e-10 * np.abs(u[0]).max())
