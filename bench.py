@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Benchmark of the panel-interaction hot path on one GB300 (or N replicas).
+
+Workload (one "step"): the multi-domain device -- conductor sphere R=1 at V0=1,
+floating torus (R=2, r=0.3) with its charge-neutrality row, dielectric
+cylinder eps_r=4 -- meshed with about 20k flat triangles (seeded), then
+  1. the matrix-free solve: GMRES on the mixed-precision matvec (FP32 regular
+     pairs, FP64 near pairs and Arnoldi) inside an FP64 iterative refinement to
+     a relative residual of 1e-8,
+  2. the surface field E+ at every centroid,
+  3. phi and E at 1e5 points uniform in [-4,4]^3 outside the conductors.
+Metric: Ginteractions/s = (target, triangle) pairs evaluated by all kernel
+launches of the step / step time (whole job over all ranks).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES solve+field-eval time & Ginteractions/s, FP64 vs mixed on GB300 at rel err 1e-6"
+UNIT = "Ginteractions/s"
+FLOPS_PER_PAIR_OP = 18        # phi+E per (target, quadrature node): see the design doc
+FP32_LANES_PER_SM = 128
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="mesh scale (1.0: ~20k triangles)")
+    ap.add_argument("--points", type=int, default=100000)
+    ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--mode", default="step", choices=["step", "matvec"],
+                    help="matvec: only W+K mixed matvecs of the workload (a small case for ncu)")
+    return ap.parse_args()
+
+
+def run_matvec(args):
+    """W + K mixed-precision matrix-free products on the workload's mesh."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2003_12663_gb300 import bem
+    mesh, _ = workload(args)
+    ctx = bem.Context(mesh)
+    x = torch.randn(ctx.nunk, dtype=torch.float64, device="cuda", generator=None)
+    for _ in range(args.warmup + args.steps):
+        ctx.matvec(x, bem.MIXED)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "matvec", "triangles": ctx.np, "launches": ctx.counters()["kernel_launches"]}))
+    ctx.close()
+
+
+def workload(args):
+    from paper_2003_12663_gb300 import meshgen as mg
+    mesh = mg.device_mesh(scale=args.scale, seed=2)
+    pts = mg.device_box_points(args.points, seed=5)
+    return mesh, pts
+
+
+def config_of(args, mesh, extra=None):
+    cfg = {"workload": "multi-domain device (conductor sphere, floating torus, dielectric cylinder)",
+           "triangles": int(mesh.np_), "unknowns": int(mesh.n_unknowns),
+           "counts_sphere_torus_cylinder": list(mesh.info["counts"]),
+           "eval_points": int(args.points), "gmres_tol": TOL, "solver": "GMRES(100)+FP64 refinement",
+           "far_rule": "3x3 Duffy/Gauss, eta=4", "l2": "flushed (256 MB write) before every step",
+           "parallelism": f"replicas x{args.gpus}"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    return dist if world > 1 else None
+
+
+def dist_max(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ roofline inputs
+def fp32_peak_tflops(num_sms):
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flop (FFMA) x max SM clock."""
+    mhz = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            mhz = float(json.load(open(p)).get("sm_max_mhz"))
+        except Exception:
+            mhz = None
+    if not mhz:
+        mhz = 2070.0
+    return num_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def far_kernel_hash():
+    src = os.path.join(ROOT, "paper_2003_12663_gb300", "csrc", "far.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the FP32 regular-pair kernel from the committed ncu
+    summary, if it was taken on the current far.cu (else None)."""
+    p = os.path.join(ROOT, "profiles", "far32_device20k.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
+    if vals.get("far.cu sha256[:16]") != far_kernel_hash():
+        return None
+    try:
+        return float(vals["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_rate(mesh, seconds, seed=0):
+    """Oracle throughput (pairs/s) on a bounded sample: the pair integrals of a
+    seeded sample of collocation rows against all triangles (classification,
+    Duffy/Gauss rule, closed form), OpenMP on all host cores."""
+    from oracle import oracle as O
+    P = O.Problem(mesh, eta=4.0, g=3)
+    rng = np.random.default_rng(seed)
+    rows = 16
+    t = 0.0
+    while True:
+        idx = np.sort(rng.choice(P.N, size=min(rows, P.N), replace=False))
+        t0 = time.perf_counter()
+        P.pair_block(P.centroids[idx], idx)
+        t = time.perf_counter() - t0
+        if t > seconds / 4 or rows >= P.N:
+            break
+        rows *= 2
+    # the timed sample
+    idx = np.sort(rng.choice(P.N, size=min(rows * 2, P.N), replace=False))
+    t0 = time.perf_counter()
+    P.pair_block(P.centroids[idx], idx)
+    t = time.perf_counter() - t0
+    pairs = len(idx) * P.N
+    return pairs / t, len(idx), t
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    dist_barrier(dist)
+    __graft_entry__.build()
+    from paper_2003_12663_gb300 import bem
+
+    mesh, pts = workload(args)
+    dev = torch.device("cuda", local)
+    ctx = bem.Context(mesh, timing=1)
+    Q = ctx.params.far_order ** 2
+    pts_d = torch.tensor(pts, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def step():
+        u, it, rel = ctx.solve(bem.MIXED, tol=TOL)
+        Es = ctx.surface_field(u[0], bem.MIXED)
+        phi, E = ctx.eval_field(u[0], pts_d, bem.MIXED)
+        out.update(u=u, it=it, rel=rel, Es=Es, phi=phi, E=E)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.reset_counters()
+    clocks = ClockSampler(local) if local == 0 else None
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if clocks:
+        clocks.start()
+    dist_barrier(dist)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.add_(1.0)
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(dist)
+    clk = clocks.stop() if clocks else None
+    times = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    ms = dist_max(dist, float(np.mean(times)), dev)
+    cnt = ctx.counters()
+    pairs_step = (cnt["pairs"][0] + cnt["pairs"][1]) / args.steps
+    value = world * pairs_step / (ms * 1e-3) / 1e9
+    launches = cnt["kernel_launches"]
+
+    # roofline of the dominant kernel: the FP32 regular-pair kernel
+    props = torch.cuda.get_device_properties(dev)
+    peak, mhz = fp32_peak_tflops(props.multi_processor_count)
+    far_pairs = cnt["pairs"][1] - cnt["near_pairs"][1]
+    flops = FLOPS_PER_PAIR_OP * Q * far_pairs
+    far_ms = cnt["far_ms"][1]
+    achieved = flops / (far_ms * 1e-3) / 1e12 if far_ms > 0 else None
+    n_launch = max(cnt["far_launches"][1], 1)
+    traffic = committed_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "kernel": "k_far32 (FP32 regular pairs, phi+E)",
+                "peak_basis": f"derived FP32 peak: {props.multi_processor_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz",
+                "flops_per_launch": flops / n_launch, "avg_launch_ms": far_ms / n_launch,
+                "fp64_far_ms_per_step": cnt["far_ms"][0] / args.steps,
+                "fp32_far_ms_per_step": far_ms / args.steps}
+
+    # accuracy of the step's solve (FP64 residual from the solver)
+    rel = out["rel"][0]
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32 regular pairs + f64",
+              "data": "synthetic (seeded meshes and points)",
+              "config": config_of(args, mesh, {"gmres_iters_per_step": cnt["gmres_iters"] / args.steps,
+                                               "fp64_relres": rel,
+                                               "pairs_per_step": pairs_step}),
+              "roofline": roofline, "gpu_launches": launches}
+    if clk:
+        result["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+
+    # the plain FP64 form of the same step, once (context for the mixed-precision claim)
+    if not args.no_fp64_form and rank == 0:
+        ctx.reset_counters()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u64, it64, rel64 = ctx.solve(bem.FP64, tol=TOL)
+        ctx.surface_field(u64[0], bem.FP64)
+        ctx.eval_field(u64[0], pts_d, bem.FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c64 = ctx.counters()
+        ms64 = e0.elapsed_time(e1)
+        du = (torch.linalg.norm(out["u"][0] - u64[0]) / torch.linalg.norm(u64[0])).item()
+        dE = ((out["E"] - ctx.eval_field(u64[0], pts_d, bem.FP64)[1]).abs().max()
+              / out["E"].abs().max()).item()
+        result["fp64_form"] = {"ms_per_step": ms64, "gmres_iters": it64, "relres": rel64[0],
+                               "value": (c64["pairs"][0] + c64["pairs"][1]) / (ms64 * 1e-3) / 1e9,
+                               "mixed_speedup": ms64 / ms,
+                               "sigma_rel_l2_mixed_vs_fp64": du, "E_rel_mixed_vs_fp64": dE}
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        X_h = torch.tensor(pts).pin_memory()
+        phi_h = torch.empty(args.points, dtype=torch.float64).pin_memory()
+        E_h = torch.empty((args.points, 3), dtype=torch.float64).pin_memory()
+        Es_h = torch.empty((mesh.np_, 3), dtype=torch.float64).pin_memory()
+        u_h = torch.empty(mesh.n_unknowns, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            c2 = bem.Context(mesh)           # host mesh -> device inside bem_create
+            p_d = X_h.to(dev, non_blocking=True)
+            u, it, rel = c2.solve(bem.MIXED, tol=TOL)
+            Es = c2.surface_field(u[0], bem.MIXED)
+            phi, E = c2.eval_field(u[0], p_d, bem.MIXED)
+            u_h.copy_(u[0], non_blocking=True)
+            Es_h.copy_(Es, non_blocking=True)
+            phi_h.copy_(phi, non_blocking=True)
+            E_h.copy_(E, non_blocking=True)
+            torch.cuda.synchronize()
+            c2.close()
+
+        e2e_step()
+        n_e2e = max(2, min(args.steps, 3))
+        dist_barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            flush.add_(1.0)
+            e2e_step()
+        torch.cuda.synchronize()
+        dist_barrier(dist)
+        e2e_ms = dist_max(dist, (time.perf_counter() - t0) * 1e3 / n_e2e, dev)
+        h2d = mesh.X.size * 8 + mesh.tri.size * 4 + mesh.region.size * 4 + pts.size * 8
+        d2h = mesh.n_unknowns * 8 + mesh.np_ * 24 + args.points * 32
+        result["e2e"] = {"value": world * pairs_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                         "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d),
+                         "d2h_bytes_per_step": int(d2h),
+                         "includes": "bem_create from host mesh, H2D points, solve, surface field, eval, D2H"}
+
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        rate, rows, secs = cpu_oracle_rate(mesh, args.cpu_seconds)
+        result["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": os.cpu_count(),
+                                  "kind": "oracle",
+                                  "sample": f"oracle pair integrals (classification, Duffy/Gauss, closed form; "
+                                            f"FP64, OpenMP) of {rows} seeded collocation rows x {mesh.np_} "
+                                            f"triangles, {secs:.1f} s"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    mesh, pts = workload(args)
+    from oracle import oracle as O
+    P = O.Problem(mesh, eta=4.0, g=3)
+    rng = np.random.default_rng(7)
+    rows = 48
+    ppts = 48
+
+    def step():
+        idx = np.sort(rng.choice(P.N, size=rows, replace=False))
+        P.pair_block(P.centroids[idx], idx)            # collocation rows (solve)
+        sel = rng.choice(len(pts), size=ppts, replace=False)
+        P.field(np.ones(P.N), pts[sel])                # field evaluation
+        return (rows + ppts) * P.N
+
+    for _ in range(args.warmup):
+        step()
+    times, pairs = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pairs = step()
+        times.append(time.perf_counter() - t0)
+    ms = float(np.mean(times)) * 1e3
+    value = pairs / (ms * 1e-3) / 1e9
+    sample = (f"per step: oracle pair integrals of {rows} seeded collocation rows and {ppts} "
+              f"evaluation points x {P.N} triangles (FP64, OpenMP)")
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "f64", "data": "synthetic (seeded meshes and points)",
+                      "config": config_of(args, mesh), "impl": "reference",
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                                       "kind": "oracle", "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    elif a.mode == "matvec":
+        run_matvec(a)
+    else:
+        run_ours(a)

@@ -87,9 +87,21 @@ typedef struct {
     int32_t max_iters;       /* total GMRES iteration limit per solve; default 2000 */
     int32_t max_refine;      /* BEM_MIXED: iterative-refinement steps; default 6 */
     int64_t max_points;      /* largest M of one bem_eval_field chunk; default 131072 */
-    int32_t near_cap;        /* most near pairs one evaluation point may have; default 1024 */
+    int32_t timing;          /* != 0: time every regular-pair kernel with CUDA events (bem_counters) */
     int32_t reserved;
 } bem_params;
+
+/* Work done by a context since creation or the last bem_reset_counters.
+ * Index [BEM_FP64] / [BEM_MIXED] of the regular-pair pass. */
+typedef struct {
+    int64_t kernel_launches;    /* CUDA kernels this library launched */
+    int64_t far_launches[2];    /* regular-pair kernel launches */
+    int64_t pairs[2];           /* (target, triangle) pairs those launches covered, M x N each */
+    int64_t near_pairs[2];      /* of those, pairs classified near and taken by the closed form */
+    double far_ms[2];           /* summed regular-pair kernel time in ms (params.timing != 0) */
+    int64_t matvecs[2];         /* matrix-free products, solver-internal ones included */
+    int64_t gmres_iters;        /* Arnoldi steps */
+} bem_counters;
 
 typedef struct bem_ctx bem_ctx;
 
@@ -122,6 +134,12 @@ int bem_sizes(const bem_ctx* ctx, int64_t* n_panels, int64_t* n_unknowns, int64_
 /* Wait for the context's stream; returns BEM_ERR_TIMEOUT if a device-side wait
  * gave up since the last call, else BEM_OK or BEM_ERR_CUDA. */
 int bem_sync(bem_ctx* ctx);
+
+/* Copy the work counters into *out (host).  Synchronises the stream. */
+int bem_get_counters(bem_ctx* ctx, bem_counters* out);
+
+/* Zero the work counters. */
+int bem_reset_counters(bem_ctx* ctx);
 
 /*
  * Rows [row0, row1) of the dense collocation matrix A of Eqs. Final1-Final4
@@ -178,7 +196,6 @@ int bem_solve(bem_ctx* ctx, int32_t precision, int32_t nrhs, const double* V0_de
  * triangle's normal field.  u_dev: device double [>= N] (entries >= N ignored);
  * pts_dev: device double [M][3]; phi_dev: device double [M] or NULL; E_dev:
  * device double [M][3] or NULL.  Any M >= 0 (processed in chunks of max_points).
- * BEM_ERR_CAPACITY if a point has more than near_cap near triangles.
  */
 int bem_eval_field(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t M,
                    const double* pts_dev, double* phi_dev, double* E_dev);

@@ -47,7 +47,21 @@ class bem_params(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("far_order", ctypes.c_int32),
                 ("gmres_restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("max_points", ctypes.c_int64),
-                ("near_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class bem_counters(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("far_launches", ctypes.c_int64 * 2),
+                ("pairs", ctypes.c_int64 * 2), ("near_pairs", ctypes.c_int64 * 2),
+                ("far_ms", ctypes.c_double * 2), ("matvecs", ctypes.c_int64 * 2),
+                ("gmres_iters", ctypes.c_int64)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
 
 
 _vp = ctypes.c_void_p
@@ -60,6 +74,8 @@ _SIGS = {
     "bem_sizes": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                          ctypes.POINTER(_i64)]),
     "bem_sync": (_i32, [_vp]),
+    "bem_get_counters": (_i32, [_vp, ctypes.POINTER(bem_counters)]),
+    "bem_reset_counters": (_i32, [_vp]),
     "bem_assemble_rows": (_i32, [_vp, _i64, _i64, _i32, _vp, _i64]),
     "bem_matvec": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "bem_rhs": (_i32, [_vp, _i32, _vp, _vp]),
@@ -164,6 +180,14 @@ class Context:
 
     def sync(self):
         _check(lib().bem_sync(self.h), self.h)
+
+    def counters(self) -> dict:
+        c = bem_counters()
+        _check(lib().bem_get_counters(self.h, ctypes.byref(c)), self.h)
+        return c.as_dict()
+
+    def reset_counters(self):
+        _check(lib().bem_reset_counters(self.h), self.h)
 
     def rhs(self, V0=None, nrhs=1):
         t = self._torch

@@ -88,8 +88,20 @@ struct bem_ctx {
     double* hcol_host = nullptr;   // pinned mirror
     int* d_status = nullptr;       // device-side status word
 
+    // work counters (bem_counters) and optional kernel timing
+    bem_counters cnt{};
+    int64_t nnz_prec[2] = {0, 0};             // near pairs of the centroids per precision
+    unsigned long long* d_near_count = nullptr;  // [2] near pairs met by the point kernels
+    std::vector<cudaEvent_t> ev0, ev1;        // timing pool: start / stop of far launches
+    std::vector<int> ev_prec;
+    size_t ev_used = 0;
+
     std::string err;
 };
+
+// timing of the regular-pair launches (setup.cu)
+void timing_begin(bem_ctx* ctx, int precision);
+void timing_end(bem_ctx* ctx);
 
 // ---------------------------------------------------------------- error helpers
 int set_err(bem_ctx* ctx, int code, const char* fmt, ...);
@@ -99,7 +111,12 @@ int set_err(bem_ctx* ctx, int code, const char* fmt, ...);
         if (e_ != cudaSuccess)                                                               \
             return set_err((ctx), BEM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
-#define BEM_LAUNCH_CHECK(ctx) BEM_CUDA_TRY(ctx, cudaGetLastError())
+// after every kernel launch: count it and report a launch error
+#define BEM_LAUNCH_CHECK(ctx)                       \
+    do {                                            \
+        ++(ctx)->cnt.kernel_launches;               \
+        BEM_CUDA_TRY(ctx, cudaGetLastError());      \
+    } while (0)
 
 // ---------------------------------------------------------------- device helpers
 // The pair classification of Sec. 4, written once per precision with explicit

@@ -269,10 +269,15 @@ int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u
                int64_t ustride, int splits, double* part)
 {
     if (T.M <= 0) return BEM_OK;
+    const int pi = precision == BEM_MIXED ? BEM_MIXED : BEM_FP64;
     for (int r = 0; r < nrhs; ++r) {
         const double* ur = u + r * ustride;
         double* pr = part + (size_t)r * splits * T.M * 4;
         int rc;
+        ctx->cnt.far_launches[pi] += 1;
+        ctx->cnt.pairs[pi] += T.M * ctx->np;
+        if (T.tpts == nullptr) ctx->cnt.near_pairs[pi] += ctx->nnz_prec[pi];  // centroid targets
+        timing_begin(ctx, pi);
         switch (ctx->g) {
             case 1: rc = launch_q<1>(ctx, precision, T, ur, splits, pr); break;
             case 2: rc = launch_q<4>(ctx, precision, T, ur, splits, pr); break;
@@ -282,6 +287,7 @@ int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u
             case 6: rc = launch_q<36>(ctx, precision, T, ur, splits, pr); break;
             default: return set_err(ctx, BEM_ERR_ARG, "far_order %d not compiled", ctx->g);
         }
+        timing_end(ctx);
         if (rc) return rc;
     }
     return BEM_OK;

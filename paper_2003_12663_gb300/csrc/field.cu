@@ -112,7 +112,7 @@ __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* _
                               const float4* __restrict__ hdr32, const double4* __restrict__ hdr64,
                               const double* __restrict__ geo, const double* __restrict__ u,
                               const double* __restrict__ part, double* __restrict__ phi,
-                              double* __restrict__ E)
+                              double* __restrict__ E, unsigned long long* __restrict__ near_count)
 {
     constexpr int WARPS = 4;
     __shared__ int32_t s_list[WARPS][64];
@@ -123,7 +123,7 @@ __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* _
     const double x = pts[3 * t], y = pts[3 * t + 1], z = pts[3 * t + 2];
     const float xf = __double2float_rn(x), yf = __double2float_rn(y), zf = __double2float_rn(z);
     double p = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-    int n = 0;
+    int n = 0, total = 0;
     auto flush = [&](int cnt) {
         if (lane < cnt) {
             const int32_t j = s_list[w][lane];
@@ -143,6 +143,7 @@ __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* _
         const unsigned m = __ballot_sync(0xffffffffu, near);
         if (near) s_list[w][n + __popc(m & ((1u << lane) - 1u))] = (int32_t)j;
         n += __popc(m);
+        total += __popc(m);
         __syncwarp();
         if (n >= 32) {
             flush(32);
@@ -163,6 +164,7 @@ __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* _
     ey = warp_sum(ey) + kInv4Pi * warp_sum(fy);
     ez = warp_sum(ez) + kInv4Pi * warp_sum(fz);
     if (lane == 0) {
+        atomicAdd(near_count, (unsigned long long)total);
         if (phi) phi[t] = p;
         if (E) { E[3 * t] = ex; E[3 * t + 1] = ey; E[3 * t + 2] = ez; }
     }
@@ -387,6 +389,7 @@ int matvec_impl(bem_ctx* c, int precision, int nrhs, const double* x, double* y)
     FarTargets T{c->tgt32, c->tgt64, nullptr, np};
     int rc = launch_far(c, precision, T, x, nrhs, n, splits, c->part);
     if (rc) return rc;
+    c->cnt.matvecs[precision == BEM_MIXED ? BEM_MIXED : BEM_FP64] += nrhs;
     const uint8_t bit = precision == BEM_MIXED ? 1 : 2;
     for (int r = 0; r < nrhs; ++r) {
         const double* pr = c->part + (size_t)r * splits * np * 4;
@@ -470,11 +473,11 @@ extern "C" int bem_eval_field(bem_ctx* c, int32_t precision, const double* u, in
         if (precision == BEM_MIXED)
             k_points_near<true><<<blocks, 128, 0, c->stream>>>(
                 mc, c->np, splits, pts + 3 * m0, c->hdr32, c->hdr64, c->geo, u, c->part,
-                phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr);
+                phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr, c->d_near_count + BEM_MIXED);
         else
             k_points_near<false><<<blocks, 128, 0, c->stream>>>(
                 mc, c->np, splits, pts + 3 * m0, c->hdr32, c->hdr64, c->geo, u, c->part,
-                phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr);
+                phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr, c->d_near_count + BEM_FP64);
         BEM_LAUNCH_CHECK(c);
     }
     return BEM_OK;

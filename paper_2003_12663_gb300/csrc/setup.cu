@@ -312,11 +312,71 @@ static void free_ctx(bem_ctx* c)
                     c->tgt64, c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, c->region_V0,
                     c->float_rows, c->float_off, c->jinv, c->near_ptr, c->near_col, c->near_val,
                     c->near_flag, c->part, c->field, c->neut, c->pts_stage, c->V, c->wvec,
-                    c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status};
+                    c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
+                    c->d_near_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hcol_host) cudaFreeHost(c->hcol_host);
+    for (cudaEvent_t e : c->ev0)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev1)
+        if (e) cudaEventDestroy(e);
     delete c;
+}
+
+// ---------------------------------------------------------------- counters, timing
+// Events come from a fixed pool created at bem_create; when it is full, the
+// pending intervals are summed (after a stream synchronisation) and reused.
+static void timing_drain(bem_ctx* c)
+{
+    if (c->ev_used == 0) return;
+    cudaStreamSynchronize(c->stream);
+    for (size_t k = 0; k < c->ev_used; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev0[k], c->ev1[k]) == cudaSuccess)
+            c->cnt.far_ms[c->ev_prec[k]] += ms;
+        else
+            cudaGetLastError();
+    }
+    c->ev_used = 0;
+}
+
+void timing_begin(bem_ctx* c, int precision)
+{
+    if (!c->prm.timing || c->ev0.empty()) return;
+    if (c->ev_used == c->ev0.size()) timing_drain(c);
+    c->ev_prec[c->ev_used] = precision;
+    cudaEventRecord(c->ev0[c->ev_used], c->stream);
+}
+
+void timing_end(bem_ctx* c)
+{
+    if (!c->prm.timing || c->ev0.empty()) return;
+    cudaEventRecord(c->ev1[c->ev_used], c->stream);
+    ++c->ev_used;
+}
+
+extern "C" int bem_get_counters(bem_ctx* c, bem_counters* out)
+{
+    if (!c || !out) return BEM_ERR_ARG;
+    timing_drain(c);
+    BEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    unsigned long long nc[2] = {0, 0};
+    BEM_CUDA_TRY(c, cudaMemcpy(nc, c->d_near_count, sizeof nc, cudaMemcpyDeviceToHost));
+    *out = c->cnt;
+    out->near_pairs[0] += (int64_t)nc[0];
+    out->near_pairs[1] += (int64_t)nc[1];
+    return BEM_OK;
+}
+
+extern "C" int bem_reset_counters(bem_ctx* c)
+{
+    if (!c) return BEM_ERR_ARG;
+    timing_drain(c);
+    c->cnt = bem_counters{};
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 2 * sizeof(unsigned long long), c->stream));
+    BEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return BEM_OK;
 }
 
 extern "C" void bem_default_params(bem_params* p)
@@ -329,7 +389,7 @@ extern "C" void bem_default_params(bem_params* p)
     p->max_iters = 2000;
     p->max_refine = 6;
     p->max_points = 131072;
-    p->near_cap = 1024;
+    p->timing = 0;
 }
 
 extern "C" const char* bem_last_error(const bem_ctx* ctx)
@@ -429,6 +489,29 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->near_ptr, ptr.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     k_near_rows<<<wblocks, 256, 0, s>>>(np, 1, c->tgt32, c->tgt64, c->hdr32, c->hdr64, nullptr,
                                          c->near_ptr, c->near_col, c->near_flag);
+    BEM_LAUNCH_CHECK(c);
+    {
+        // near pairs per precision, for the work counters
+        std::vector<uint8_t> fl(c->nnz);
+        BEM_CUDA_TRY(c, cudaMemcpyAsync(fl.data(), c->near_flag, c->nnz, cudaMemcpyDeviceToHost, s));
+        BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
+        for (uint8_t f : fl) {
+            c->nnz_prec[BEM_MIXED] += (f & 1) ? 1 : 0;
+            c->nnz_prec[BEM_FP64] += (f & 2) ? 1 : 0;
+        }
+    }
+    if ((rc = dalloc(c, &c->d_near_count, 2))) return rc;
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 2 * sizeof(unsigned long long), s));
+    if (c->prm.timing) {
+        const int pool = 1024;
+        c->ev0.resize(pool);
+        c->ev1.resize(pool);
+        c->ev_prec.assign(pool, 0);
+        for (int k = 0; k < pool; ++k) {
+            BEM_CUDA_TRY(c, cudaEventCreate(&c->ev0[k]));
+            BEM_CUDA_TRY(c, cudaEventCreate(&c->ev1[k]));
+        }
+    }
     BEM_LAUNCH_CHECK(c);
     k_near_values<<<(unsigned)np, 64, 0, s>>>(np, c->near_ptr, c->near_col, c->geo, c->near_val);
     BEM_LAUNCH_CHECK(c);

@@ -170,6 +170,7 @@ int gmres(bem_ctx* c, int precision, const double* b, double* x, bool x_zero, do
             BEM_CUDA_TRY(c, cudaMemcpyAsync(hh, hsum, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
             BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
             ++*iters;
+            ++c->cnt.gmres_iters;
             double* Hj = &H[(size_t)j * (m + 1)];  // column j
             for (int k = 0; k <= j; ++k) Hj[k] = hh[k];
             Hj[j + 1] = std::sqrt(std::max(hh[j + 1], 0.0));
