@@ -201,6 +201,26 @@ int bem_eval_field(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t
                    const double* pts_dev, double* phi_dev, double* E_dev);
 
 /*
+ * Same result as bem_eval_field, for callers that cannot allocate device memory
+ * when they evaluate the field (for example a process whose remaining GPU memory
+ * belongs to its own arena after start-up, so that a further cudaMalloc fails or is
+ * not allowed).  The paper has no counterpart; this is a property of the library.
+ *
+ * The call allocates nothing.  Its scratch (the far-field partial sums) is one fixed
+ * 8 MiB array in the library's static device memory, which every GPU that loads the
+ * library holds until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the context's device current;
+ * make that first call before any stream capture.  All calls on a device share the
+ * array, so calls whose GPU work overlaps (other streams, other threads, other
+ * contexts on the same device) race and give wrong results: order them.  Nothing
+ * needs clearing between calls (every partial read is written by the same call).
+ * Limit: M <= 65536 points per call, else BEM_ERR_CAPACITY and no work is queued.
+ * Arguments and layout as bem_eval_field; the context's device must be current.
+ */
+int bem_eval_field_static(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t M,
+                          const double* pts_dev, double* phi_dev, double* E_dev);
+
+/*
  * Field on the + side of the surface at every centroid ("E surface" of Sec. 5):
  *   E+(c_i) = E_PV(c_i) + u_i n_i / 2   (Eq. ADL read as E+.n = sigma/2 + K' sigma).
  * E_dev: device double [N][3].

@@ -81,6 +81,7 @@ _SIGS = {
     "bem_rhs": (_i32, [_vp, _i32, _vp, _vp]),
     "bem_solve": (_i32, [_vp, _i32, _i32, _vp, _vp, _dbl, ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
     "bem_eval_field": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp]),
+    "bem_eval_field_static": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp]),
     "bem_surface_field": (_i32, [_vp, _i32, _vp, _vp]),
 }
 _lib = None
@@ -226,6 +227,20 @@ class Context:
         _check(lib().bem_eval_field(self.h, precision, _ptr(u), M, _ptr(pts),
                                     _ptr(phi if want_phi else None), _ptr(E if want_E else None)),
                self.h)
+        return phi, E
+
+    def eval_field_static(self, u, pts, precision=FP64, phi=None, E=None):
+        """bem_eval_field_static: same result as eval_field; the call itself
+        allocates nothing on the library side (scratch is a fixed static array).
+        phi and E may be passed in preallocated."""
+        t = self._torch
+        u = self._dev(u)
+        pts = self._dev(pts)
+        M = pts.shape[0]
+        phi = t.empty(M, dtype=t.float64, device="cuda") if phi is None else phi
+        E = t.empty((M, 3), dtype=t.float64, device="cuda") if E is None else E
+        _check(lib().bem_eval_field_static(self.h, precision, _ptr(u), M, _ptr(pts), _ptr(phi),
+                                           _ptr(E)), self.h)
         return phi, E
 
     def surface_field(self, u, precision=FP64):

@@ -217,6 +217,8 @@ int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u
                int64_t ustride, int splits, double* part);
 
 // field.cu
+int launch_points_near(bem_ctx* ctx, int precision, int64_t M, const double* pts, const double* u,
+                       const double* part, int splits, double* phi, double* E);
 int matvec_impl(bem_ctx* ctx, int precision, int nrhs, const double* x, double* y);
 
 // setup.cu

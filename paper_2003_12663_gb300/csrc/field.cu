@@ -454,6 +454,25 @@ extern "C" int bem_surface_field(bem_ctx* c, int32_t precision, const double* u,
     return BEM_OK;
 }
 
+// Deferred near pass + split reduction for M points whose far partial sums are in
+// part[splits][M][4] (used by the static-scratch entry point).
+int launch_points_near(bem_ctx* c, int precision, int64_t M, const double* pts, const double* u,
+                       const double* part, int splits, double* phi, double* E)
+{
+    if (M <= 0) return BEM_OK;
+    const unsigned blocks = (unsigned)((M + 3) / 4);
+    if (precision == BEM_MIXED)
+        k_points_near<true><<<blocks, 128, 0, c->stream>>>(M, c->np, splits, pts, c->hdr32,
+                                                             c->hdr64, c->geo, u, part, phi, E,
+                                                             c->d_near_count + BEM_MIXED);
+    else
+        k_points_near<false><<<blocks, 128, 0, c->stream>>>(M, c->np, splits, pts, c->hdr32,
+                                                              c->hdr64, c->geo, u, part, phi, E,
+                                                              c->d_near_count + BEM_FP64);
+    BEM_LAUNCH_CHECK(c);
+    return BEM_OK;
+}
+
 extern "C" int bem_eval_field(bem_ctx* c, int32_t precision, const double* u, int64_t M,
                               const double* pts, double* phi, double* E)
 {
