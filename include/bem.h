@@ -59,8 +59,10 @@ enum { BEM_CONDUCTOR = 0, BEM_FLOATING = 1, BEM_DIELECTRIC = 2 };
 
 /* Arithmetic of the regular (far-field) pairs.  BEM_FP64: every step in FP64.
  * BEM_MIXED: regular pairs in FP32 with compensated FP32 accumulation; the
- * closed-form near pairs, reductions and everything else in FP64. */
-enum { BEM_FP64 = 0, BEM_MIXED = 1 };
+ * closed-form near pairs, reductions and everything else in FP64.
+ * BEM_DF (bem_matvec only): the FP64 form's operator with its regular pairs in
+ * double-FP32 arithmetic (see BEM_RESIDUAL_DF), agreeing with BEM_FP64 to ~1e-13. */
+enum { BEM_FP64 = 0, BEM_MIXED = 1, BEM_DF = 2 };
 
 typedef struct {
     int32_t kind;        /* BEM_CONDUCTOR, BEM_FLOATING or BEM_DIELECTRIC */
@@ -88,18 +90,26 @@ typedef struct {
     int32_t max_refine;      /* BEM_MIXED: iterative-refinement steps; default 6 */
     int64_t max_points;      /* largest M of one bem_eval_field chunk; default 131072 */
     int32_t timing;          /* != 0: time every regular-pair kernel with CUDA events (bem_counters) */
-    int32_t reserved;
+    int32_t residual;        /* BEM_MIXED refinement residual b - A u: BEM_RESIDUAL_DF (default)
+                                or BEM_RESIDUAL_FP64 */
 } bem_params;
 
+/* How the iterative refinement of BEM_MIXED forms its residual b - A u.
+ * BEM_RESIDUAL_FP64: the FP64 regular-pair kernel.  BEM_RESIDUAL_DF: the same pairs
+ * in double-FP32 arithmetic (an unevaluated sum of two floats, error-free
+ * transformations of Dekker and Knuth) on the FP32 units, about 1e-13 relative per
+ * pair, with the pair classification of the FP64 form reproduced exactly. */
+enum { BEM_RESIDUAL_DF = 0, BEM_RESIDUAL_FP64 = 1 };
+
 /* Work done by a context since creation or the last bem_reset_counters.
- * Index [BEM_FP64] / [BEM_MIXED] of the regular-pair pass. */
+ * Index [BEM_FP64] / [BEM_MIXED] / [2] = double-FP32 residual pass. */
 typedef struct {
     int64_t kernel_launches;    /* CUDA kernels this library launched */
-    int64_t far_launches[2];    /* regular-pair kernel launches */
-    int64_t pairs[2];           /* (target, triangle) pairs those launches covered, M x N each */
-    int64_t near_pairs[2];      /* of those, pairs classified near and taken by the closed form */
-    double far_ms[2];           /* summed regular-pair kernel time in ms (params.timing != 0) */
-    int64_t matvecs[2];         /* matrix-free products, solver-internal ones included */
+    int64_t far_launches[3];    /* regular-pair kernel launches */
+    int64_t pairs[3];           /* (target, triangle) pairs those launches covered, M x N each */
+    int64_t near_pairs[3];      /* of those, pairs classified near and taken by the closed form */
+    double far_ms[3];           /* summed regular-pair kernel time in ms (params.timing != 0) */
+    int64_t matvecs[3];         /* matrix-free products, solver-internal ones included */
     int64_t gmres_iters;        /* Arnoldi steps */
 } bem_counters;
 
@@ -162,6 +172,7 @@ int bem_assemble_rows(bem_ctx* ctx, int64_t row0, int64_t row1, int32_t precisio
  * y = A x without forming A (matrix-free): far pairs by the quadrature kernel,
  * near pairs from the precomputed closed-form values, then the row equations
  * above.  x_dev, y_dev: device double [nrhs][N+F].  1 <= nrhs <= 4.
+ * precision: BEM_FP64, BEM_MIXED or BEM_DF.
  */
 int bem_matvec(bem_ctx* ctx, int32_t precision, int32_t nrhs, const double* x_dev, double* y_dev);
 

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbem.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "bem.h")
 
-FP64, MIXED = 0, 1
+FP64, MIXED, DF = 0, 1, 2
 CONDUCTOR, FLOATING, DIELECTRIC = 0, 1, 2
 _KIND = {"conductor": CONDUCTOR, "floating": FLOATING, "dielectric": DIELECTRIC}
 
@@ -47,13 +47,16 @@ class bem_params(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("far_order", ctypes.c_int32),
                 ("gmres_restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("max_points", ctypes.c_int64),
-                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("residual", ctypes.c_int32)]
+
+
+RESIDUAL_DF, RESIDUAL_FP64 = 0, 1
 
 
 class bem_counters(ctypes.Structure):
-    _fields_ = [("kernel_launches", ctypes.c_int64), ("far_launches", ctypes.c_int64 * 2),
-                ("pairs", ctypes.c_int64 * 2), ("near_pairs", ctypes.c_int64 * 2),
-                ("far_ms", ctypes.c_double * 2), ("matvecs", ctypes.c_int64 * 2),
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("far_launches", ctypes.c_int64 * 3),
+                ("pairs", ctypes.c_int64 * 3), ("near_pairs", ctypes.c_int64 * 3),
+                ("far_ms", ctypes.c_double * 3), ("matvecs", ctypes.c_int64 * 3),
                 ("gmres_iters", ctypes.c_int64)]
 
     def as_dict(self):

@@ -25,6 +25,7 @@ enum { GEO_A = 0, GEO_B = 3, GEO_C = 6, GEO_N = 9, GEO_AREA = 12, GEO_CTR = 13, 
 
 constexpr int kMaxOrder = 6;          // largest far_order g
 constexpr int kMaxRhs = 4;            // right-hand sides per matvec launch
+constexpr int kPrecDF = BEM_DF;       // regular pairs in double-FP32 arithmetic
 constexpr double kInv4Pi = 0.07957747154594767;  // 1/(4 pi)
 
 struct bem_ctx {
@@ -47,6 +48,8 @@ struct bem_ctx {
     double4* hdr64 = nullptr;   // [np] (cc, (eta R)^2)    FP64
     float4* node32 = nullptr;   // [np][Q] (y, w)          FP32
     double4* node64 = nullptr;  // [np][Q] (y, w)          FP64
+    float4* node_lo32 = nullptr;  // [np][Q] node - node32 (low parts of the double-FP32 nodes)
+    float4* tgt_lo32 = nullptr;   // [np] centroid - tgt32
     float4* tgt32 = nullptr;    // [np] centroids          FP32
     double4* tgt64 = nullptr;   // [np] centroids          FP64
 
@@ -66,6 +69,7 @@ struct bem_ctx {
     int64_t* near_ptr = nullptr;   // [np+1]
     int32_t* near_col = nullptr;   // [nnz]
     double4* near_val = nullptr;   // [nnz] exact (S, G) of the pair, G's normal part PV for i==j
+    double4* near_val_df = nullptr;  // [nnz] what the double-FP32 pass adds (see k_near_values)
     uint8_t* near_flag = nullptr;  // [nnz] bit0: near in FP32 classification, bit1: in FP64
 
     // workspace
@@ -90,7 +94,7 @@ struct bem_ctx {
 
     // work counters (bem_counters) and optional kernel timing
     bem_counters cnt{};
-    int64_t nnz_prec[2] = {0, 0};             // near pairs of the centroids per precision
+    int64_t nnz_prec[3] = {0, 0, 0};          // near pairs of the centroids per pass
     unsigned long long* d_near_count = nullptr;  // [2] near pairs met by the point kernels
     std::vector<cudaEvent_t> ev0, ev1;        // timing pool: start / stop of far launches
     std::vector<int> ev_prec;
@@ -208,6 +212,7 @@ __device__ __forceinline__ void tri_closed_form(const double* __restrict__ gp, d
 // (split, target) record of 4 doubles per right-hand side.
 struct FarTargets {
     const float4* t32;       // FP32 targets (x,y,z,-) or nullptr
+    const float4* t32lo;     // low parts for the double-FP32 pass (centroid targets only)
     const double4* t64;      // FP64 targets (x,y,z,-) or nullptr
     const double* tpts;      // or raw double [M][3]
     int64_t M;

@@ -25,6 +25,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kTR32 = 4;
 constexpr int kTR64 = 2;
+constexpr int kTRdf = 2;
 constexpr int kPC32 = 32;
 constexpr int kPC64 = 16;
 
@@ -221,6 +222,164 @@ k_far64(const double4* __restrict__ t64, const double* __restrict__ tpts, int64_
     }
 }
 
+// ---------------------------------------------------------------- double-FP32
+// A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2).  The
+// operations are the error-free transformations of Knuth (two-sum) and Dekker
+// (two-product, here with an FMA), written with explicit-rounding intrinsics so
+// that the compiler cannot fuse or reorder them.
+struct df32 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df32 quick_two_sum(float a, float b)  // needs |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df32 df_add(df32 a, df32 b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return quick_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df32 df_neg(df32 a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ df32 df_sqr(df32 a)
+{
+    const float p = __fmul_rn(a.hi, a.hi);
+    const float e = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, __fmaf_rn(a.hi, a.hi, -p));
+    return quick_two_sum(p, e);
+}
+
+// 1/sqrt(x): the FP32 estimate y, then one Newton step y + y (1 - x y^2) / 2 in
+// double-FP32 (the error goes from ~2^-22 to ~2^-44).
+__device__ __forceinline__ df32 df_rsqrt(df32 x)
+{
+    const float y = rsqrtf(x.hi);
+    const df32 yy = {__fmul_rn(y, y), __fmaf_rn(y, y, -__fmul_rn(y, y))};
+    const df32 t = df_mul(x, yy);
+    const float d = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+    return quick_two_sum(y, __fmul_rn(__fmul_rn(y, d), 0.5f));
+}
+
+__device__ __forceinline__ df32 df_from(double v)
+{
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+
+// Regular pairs in double-FP32, centroid targets only (the refinement residual).
+// Near pairs are masked with the FP32 classification, exactly as in k_far32; the
+// consumer adds per near pair the value that turns the result into the FP64
+// classification's (see k_near_values).
+template <int TR, int Q>
+__global__ void __launch_bounds__(kThreads)
+k_far_df(const float4* __restrict__ t32, const float4* __restrict__ t32lo, int64_t M,
+         const float4* __restrict__ hdr, const float4* __restrict__ node,
+         const float4* __restrict__ node_lo, const double* __restrict__ u, int64_t np,
+         int64_t per_split, double* __restrict__ part)
+{
+    constexpr int PC = 16;
+    __shared__ float4 s_hdr[PC];
+    __shared__ float2 s_u[PC];
+    __shared__ float4 s_node[PC * Q];
+    __shared__ float4 s_nlo[PC * Q];
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * TR);
+    const int split = blockIdx.y;
+    const int64_t p0 = (int64_t)split * per_split;
+    const int64_t p1 = min(np, p0 + per_split);
+
+    df32 tx[TR], ty[TR], tz[TR];
+    float fx[TR], fy[TR], fz[TR];  // FP32 targets of the classification
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int64_t t = min(base + r * kThreads + tid, M - 1);
+        const float4 h = t32[t], l = t32lo[t];
+        tx[r] = {h.x, l.x}; ty[r] = {h.y, l.y}; tz[r] = {h.z, l.z};
+        fx[r] = h.x; fy[r] = h.y; fz[r] = h.z;
+    }
+    df32 acc[TR][4];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = {0.f, 0.f};
+
+    for (int64_t c0 = p0; c0 < p1; c0 += PC) {
+        const int npc = (int)min((int64_t)PC, p1 - c0);
+        __syncthreads();
+        for (int k = tid; k < npc; k += kThreads) {
+            s_hdr[k] = hdr[c0 + k];
+            const df32 v = df_from(u[c0 + k]);
+            s_u[k] = make_float2(v.hi, v.lo);
+        }
+        for (int k = tid; k < npc * Q; k += kThreads) {
+            s_node[k] = node[c0 * Q + k];
+            s_nlo[k] = node_lo[c0 * Q + k];
+        }
+        __syncthreads();
+        for (int p = 0; p < npc; ++p) {
+            df32 ps[TR], gx[TR], gy[TR], gz[TR];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const float4 nh = s_node[p * Q + k], nl = s_nlo[p * Q + k];
+                const df32 w = {nh.w, nl.w};
+#pragma unroll
+                for (int r = 0; r < TR; ++r) {
+                    const df32 dx = df_add(tx[r], df_neg({nh.x, nl.x}));
+                    const df32 dy = df_add(ty[r], df_neg({nh.y, nl.y}));
+                    const df32 dz = df_add(tz[r], df_neg({nh.z, nl.z}));
+                    df32 r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+                    r2.hi = fmaxf(r2.hi, 1e-20f);
+                    const df32 ri = df_rsqrt(r2);
+                    const df32 t = df_mul(w, ri);
+                    const df32 t3 = df_mul(t, df_sqr(ri));
+                    if (k == 0) {
+                        ps[r] = t;
+                        gx[r] = df_mul(t3, dx); gy[r] = df_mul(t3, dy); gz[r] = df_mul(t3, dz);
+                    } else {
+                        ps[r] = df_add(ps[r], t);
+                        gx[r] = df_add(gx[r], df_mul(t3, dx));
+                        gy[r] = df_add(gy[r], df_mul(t3, dy));
+                        gz[r] = df_add(gz[r], df_mul(t3, dz));
+                    }
+                }
+            }
+            const float4 h = s_hdr[p];
+            const float2 up = s_u[p];
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const bool far = is_far32(fx[r], fy[r], fz[r], h);
+                const df32 m = far ? df32{up.x, up.y} : df32{0.f, 0.f};
+                acc[r][0] = df_add(acc[r][0], df_mul(m, ps[r]));
+                acc[r][1] = df_add(acc[r][1], df_mul(m, gx[r]));
+                acc[r][2] = df_add(acc[r][2], df_mul(m, gy[r]));
+                acc[r][3] = df_add(acc[r][3], df_mul(m, gz[r]));
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int64_t t = base + r * kThreads + tid;
+        if (t < M) {
+            double* o = part + ((int64_t)split * M + t) * 4;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) o[c] = (double)acc[r][c].hi + (double)acc[r][c].lo;
+        }
+    }
+}
+
 template <int Q>
 int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, int splits,
              double* part)
@@ -228,7 +387,12 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
     const int64_t np = ctx->np;
     const int64_t per_split = (np + splits - 1) / splits;
     const bool raw = (T.tpts != nullptr);
-    if (precision == BEM_MIXED) {
+    if (precision == kPrecDF) {
+        if (raw || !T.t32lo) return set_err(ctx, BEM_ERR_ARG, "double-FP32 pass needs centroid targets");
+        dim3 grid((unsigned)((T.M + kThreads * kTRdf - 1) / (kThreads * kTRdf)), (unsigned)splits);
+        k_far_df<kTRdf, Q><<<grid, kThreads, 0, ctx->stream>>>(
+            T.t32, T.t32lo, T.M, ctx->hdr32, ctx->node32, ctx->node_lo32, u, np, per_split, part);
+    } else if (precision == BEM_MIXED) {
         dim3 grid((unsigned)((T.M + kThreads * kTR32 - 1) / (kThreads * kTR32)), (unsigned)splits);
         if (raw)
             k_far32<kTR32, Q, true><<<grid, kThreads, 0, ctx->stream>>>(
@@ -255,7 +419,7 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
 // four, but no slice shorter than two staging chunks.
 int far_splits(const bem_ctx* ctx, int precision, int64_t M)
 {
-    const int tr = precision == BEM_MIXED ? kTR32 : kTR64;
+    const int tr = precision == BEM_MIXED ? kTR32 : (precision == kPrecDF ? kTRdf : kTR64);
     const int pc = precision == BEM_MIXED ? kPC32 : kPC64;
     const int64_t tiles = (M + kThreads * tr - 1) / (kThreads * tr);
     const int64_t slots = (int64_t)std::max(ctx->num_sms, 1) * 4;
@@ -269,7 +433,7 @@ int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u
                int64_t ustride, int splits, double* part)
 {
     if (T.M <= 0) return BEM_OK;
-    const int pi = precision == BEM_MIXED ? BEM_MIXED : BEM_FP64;
+    const int pi = precision;  // BEM_FP64, BEM_MIXED or kPrecDF
     for (int r = 0; r < nrhs; ++r) {
         const double* ur = u + r * ustride;
         double* pr = part + (size_t)r * splits * T.M * 4;

@@ -386,15 +386,18 @@ int matvec_impl(bem_ctx* c, int precision, int nrhs, const double* x, double* y)
     const int splits = far_splits(c, precision, np);
     if ((size_t)splits * np * 4 * nrhs > c->part_cap)
         return set_err(c, BEM_ERR_CAPACITY, "far workspace too small");
-    FarTargets T{c->tgt32, c->tgt64, nullptr, np};
+    FarTargets T{c->tgt32, c->tgt_lo32, c->tgt64, nullptr, np};
     int rc = launch_far(c, precision, T, x, nrhs, n, splits, c->part);
     if (rc) return rc;
-    c->cnt.matvecs[precision == BEM_MIXED ? BEM_MIXED : BEM_FP64] += nrhs;
-    const uint8_t bit = precision == BEM_MIXED ? 1 : 2;
+    c->cnt.matvecs[precision] += nrhs;
+    // near pairs: the FP32 / FP64 classification's closed forms; the double-FP32
+    // pass masks like FP32 and takes the corrected values that reproduce FP64
+    const uint8_t bit = precision == BEM_MIXED ? 1 : (precision == BEM_FP64 ? 2 : 3);
+    const double4* nval = precision == kPrecDF ? c->near_val_df : c->near_val;
     for (int r = 0; r < nrhs; ++r) {
         const double* pr = c->part + (size_t)r * splits * np * 4;
         k_rows<<<(unsigned)((np * 32 + 127) / 128), 128, 0, c->stream>>>(
-            np, splits, pr, c->near_ptr, c->near_col, c->near_val, c->near_flag, bit, x + r * n,
+            np, splits, pr, c->near_ptr, c->near_col, nval, c->near_flag, bit, x + r * n,
             c->geo, c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, 0, y + r * n,
             c->neut + r * np, c->field + (size_t)r * np * 4);
         BEM_LAUNCH_CHECK(c);
@@ -417,7 +420,8 @@ static int check_prec(bem_ctx* c, int precision)
 extern "C" int bem_matvec(bem_ctx* c, int32_t precision, int32_t nrhs, const double* x, double* y)
 {
     if (!c) return BEM_ERR_ARG;
-    if (int rc = check_prec(c, precision)) return rc;
+    if (precision != BEM_DF)
+        if (int rc = check_prec(c, precision)) return rc;
     if (nrhs < 1 || nrhs > kMaxRhs || !x || !y)
         return set_err(c, BEM_ERR_ARG, "bem_matvec: need 1 <= nrhs <= %d and non-NULL x, y", kMaxRhs);
     return matvec_impl(c, precision, nrhs, x, y);
@@ -443,7 +447,7 @@ extern "C" int bem_surface_field(bem_ctx* c, int32_t precision, const double* u,
     if (!u || !E) return set_err(c, BEM_ERR_ARG, "bem_surface_field: NULL pointer");
     const int64_t np = c->np;
     const int splits = far_splits(c, precision, np);
-    FarTargets T{c->tgt32, c->tgt64, nullptr, np};
+    FarTargets T{c->tgt32, c->tgt_lo32, c->tgt64, nullptr, np};
     int rc = launch_far(c, precision, T, u, 1, 0, splits, c->part);
     if (rc) return rc;
     const uint8_t bit = precision == BEM_MIXED ? 1 : 2;
@@ -485,7 +489,7 @@ extern "C" int bem_eval_field(bem_ctx* c, int32_t precision, const double* u, in
         const int splits = far_splits(c, precision, mc);
         if ((size_t)splits * mc * 4 > c->part_cap)
             return set_err(c, BEM_ERR_CAPACITY, "far workspace too small");
-        FarTargets T{nullptr, nullptr, pts + 3 * m0, mc};
+        FarTargets T{nullptr, nullptr, nullptr, pts + 3 * m0, mc};
         int rc = launch_far(c, precision, T, u, 1, 0, splits, c->part);
         if (rc) return rc;
         const unsigned blocks = (unsigned)((mc + 3) / 4);

@@ -146,6 +146,7 @@ __global__ void k_panels(int64_t np, int g, double eta, const double* __restrict
                          float4* __restrict__ hdr32, double4* __restrict__ hdr64,
                          float4* __restrict__ node32, double4* __restrict__ node64,
                          float4* __restrict__ tgt32, double4* __restrict__ tgt64,
+                         float4* __restrict__ node_lo32, float4* __restrict__ tgt_lo32,
                          int* __restrict__ status)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -202,6 +203,11 @@ __global__ void k_panels(int64_t np, int g, double eta, const double* __restrict
                            __double2float_rn(eR2));
     tgt64[j] = make_double4(cx, cy, cz, 0.0);
     tgt32[j] = make_float4(__double2float_rn(cx), __double2float_rn(cy), __double2float_rn(cz), 0.f);
+    {
+        const float4 h = tgt32[j];
+        tgt_lo32[j] = make_float4(__double2float_rn(cx - (double)h.x), __double2float_rn(cy - (double)h.y),
+                                  __double2float_rn(cz - (double)h.z), 0.f);
+    }
     const int Q = g * g;
     for (int k = 0; k < g; ++k) {
         const double uk = c_rule_u[k];
@@ -212,8 +218,12 @@ __global__ void k_panels(int64_t np, int g, double eta, const double* __restrict
             const double yz = v[2] + uk * abz + uk * vl * bcz;
             const double w = 2.0 * area * c_rule_wu[k] * c_rule_wv[l];
             node64[j * Q + k * g + l] = make_double4(yx, yy, yz, w);
-            node32[j * Q + k * g + l] = make_float4(__double2float_rn(yx), __double2float_rn(yy),
-                                                    __double2float_rn(yz), __double2float_rn(w));
+            const float4 h = make_float4(__double2float_rn(yx), __double2float_rn(yy),
+                                         __double2float_rn(yz), __double2float_rn(w));
+            node32[j * Q + k * g + l] = h;
+            node_lo32[j * Q + k * g + l] =
+                make_float4(__double2float_rn(yx - (double)h.x), __double2float_rn(yy - (double)h.y),
+                            __double2float_rn(yz - (double)h.z), __double2float_rn(w - (double)h.w));
         }
     }
 }
@@ -253,9 +263,17 @@ __global__ void k_near_rows(int64_t np, int phase, const float4* __restrict__ tg
 }
 
 // One thread per near pair: exact S and G (principal value of the own panel).
-__global__ void k_near_values(int64_t np, const int64_t* __restrict__ ptr,
-                              const int32_t* __restrict__ col, const double* __restrict__ geo,
-                              double4* __restrict__ val)
+//
+// The double-FP32 residual pass masks near pairs with the FP32 classification but
+// must reproduce the FP64 form, so its near values are
+//   val_df = [near in FP64] exact + ([far in FP64] - [far in FP32]) quad64,
+// quad64 being the FP64 Duffy/Gauss value of the pair: "exact" where both agree,
+// "exact - quad" where only FP64 calls the pair near (the pass added quad), "quad"
+// where only FP32 does (the pass skipped a pair the FP64 form integrates).
+__global__ void k_near_values(int64_t np, int Q, const int64_t* __restrict__ ptr,
+                              const int32_t* __restrict__ col, const uint8_t* __restrict__ flag,
+                              const double* __restrict__ geo, const double4* __restrict__ node64,
+                              double4* __restrict__ val, double4* __restrict__ val_df)
 {
     const int64_t i = blockIdx.x;
     const double* gi = geo + GEO_STRIDE * i;
@@ -265,6 +283,21 @@ __global__ void k_near_values(int64_t np, const int64_t* __restrict__ ptr,
         double S, Gx, Gy, Gz;
         tri_closed_form(geo + GEO_STRIDE * (int64_t)j, x, y, z, j == i, S, Gx, Gy, Gz);
         val[k] = make_double4(S, Gx, Gy, Gz);
+        const bool n32 = flag[k] & 1, n64 = flag[k] & 2;
+        double qS = 0.0, qx = 0.0, qy = 0.0, qz = 0.0;
+        if (n32 != n64) {
+            for (int q = 0; q < Q; ++q) {
+                const double4 nd = node64[(int64_t)j * Q + q];
+                const double dx = x - nd.x, dy = y - nd.y, dz = z - nd.z;
+                const double ri = rsqrt(dx * dx + dy * dy + dz * dz);
+                const double w = nd.w * ri, w3 = w * ri * ri;
+                qS += w; qx += w3 * dx; qy += w3 * dy; qz += w3 * dz;
+            }
+            qS *= kInv4Pi; qx *= kInv4Pi; qy *= kInv4Pi; qz *= kInv4Pi;
+        }
+        const double a = n64 ? 1.0 : 0.0;
+        const double b = (n64 ? 0.0 : 1.0) - (n32 ? 0.0 : 1.0);
+        val_df[k] = make_double4(a * S + b * qS, a * Gx + b * qx, a * Gy + b * qy, a * Gz + b * qz);
     }
 }
 
@@ -313,7 +346,7 @@ static void free_ctx(bem_ctx* c)
                     c->float_rows, c->float_off, c->jinv, c->near_ptr, c->near_col, c->near_val,
                     c->near_flag, c->part, c->field, c->neut, c->pts_stage, c->V, c->wvec,
                     c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
-                    c->d_near_count};
+                    c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hcol_host) cudaFreeHost(c->hcol_host);
@@ -390,6 +423,7 @@ extern "C" void bem_default_params(bem_params* p)
     p->max_refine = 6;
     p->max_points = 131072;
     p->timing = 0;
+    p->residual = BEM_RESIDUAL_DF;
 }
 
 extern "C" const char* bem_last_error(const bem_ctx* ctx)
@@ -451,14 +485,16 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         (rc = dalloc(c, &c->geo, GEO_STRIDE * np)) || (rc = dalloc(c, &c->hdr32, np)) ||
         (rc = dalloc(c, &c->hdr64, np)) || (rc = dalloc(c, &c->node32, Q * np)) ||
         (rc = dalloc(c, &c->node64, Q * np)) || (rc = dalloc(c, &c->tgt32, np)) ||
-        (rc = dalloc(c, &c->tgt64, np)) || (rc = dalloc(c, &c->d_status, 1)))
+        (rc = dalloc(c, &c->tgt64, np)) || (rc = dalloc(c, &c->d_status, 1)) ||
+        (rc = dalloc(c, &c->node_lo32, Q * np)) || (rc = dalloc(c, &c->tgt_lo32, np)))
         return rc;
     BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->X, mesh->X, 3 * nv * sizeof(double), cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->tri, mesh->tri, 3 * np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     k_panels<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(np, c->g, c->prm.eta, c->X, c->tri, c->geo,
                                                           c->hdr32, c->hdr64, c->node32, c->node64,
-                                                          c->tgt32, c->tgt64, c->d_status);
+                                                          c->tgt32, c->tgt64, c->node_lo32,
+                                                          c->tgt_lo32, c->d_status);
     BEM_LAUNCH_CHECK(c);
     int st = 0;
     BEM_CUDA_TRY(c, cudaMemcpyAsync(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
@@ -498,6 +534,7 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         for (uint8_t f : fl) {
             c->nnz_prec[BEM_MIXED] += (f & 1) ? 1 : 0;
             c->nnz_prec[BEM_FP64] += (f & 2) ? 1 : 0;
+            c->nnz_prec[kPrecDF] += (f & 1) ? 1 : 0;  // masked like FP32
         }
     }
     if ((rc = dalloc(c, &c->d_near_count, 2))) return rc;
@@ -513,7 +550,9 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         }
     }
     BEM_LAUNCH_CHECK(c);
-    k_near_values<<<(unsigned)np, 64, 0, s>>>(np, c->near_ptr, c->near_col, c->geo, c->near_val);
+    if ((rc = dalloc(c, &c->near_val_df, c->nnz))) return rc;
+    k_near_values<<<(unsigned)np, 64, 0, s>>>(np, Q, c->near_ptr, c->near_col, c->near_flag, c->geo,
+                                               c->node64, c->near_val, c->near_val_df);
     BEM_LAUNCH_CHECK(c);
 
     // rows
@@ -618,7 +657,8 @@ extern "C" int bem_create(bem_ctx** out, const bem_mesh* mesh, const bem_params*
         bem_default_params(&prm);
     if (!(prm.eta >= 1.0) || prm.far_order < 1 || prm.far_order > kMaxOrder ||
         prm.gmres_restart < 1 || prm.gmres_restart > 1000 || prm.max_iters < 1 ||
-        prm.max_refine < 1 || prm.max_points < 1)
+        prm.max_refine < 1 || prm.max_points < 1 ||
+        (prm.residual != BEM_RESIDUAL_DF && prm.residual != BEM_RESIDUAL_FP64))
         return set_err(nullptr, BEM_ERR_ARG, "bad parameters (need eta >= 1, 1 <= far_order <= %d)",
                        kMaxOrder);
     for (int64_t i = 0; i < 3 * mesh->np; ++i)

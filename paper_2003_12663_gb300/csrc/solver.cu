@@ -1,7 +1,8 @@
 // solver.cu -- restarted GMRES with right Jacobi scaling (Sec. 3: Krylov methods
 // need only matrix-vector products; Sec. 5: GMRES with a diagonal
 // preconditioner) on the matrix-free matvec, and, for BEM_MIXED, an iterative
-// refinement whose residual b - A u is formed with the FP64 matvec.
+// refinement whose residual b - A u is formed with the FP64 form's operator (in
+// double-FP32 arithmetic by default, or with the FP64 kernel).
 //
 // The Krylov basis, the orthogonalisation (classical Gram-Schmidt applied
 // twice) and all vectors stay on the device in FP64; only the new Hessenberg
@@ -256,7 +257,8 @@ extern "C" int bem_solve(bem_ctx* c, int32_t precision, int32_t nrhs, const doub
             if (rc && rc != BEM_ERR_NOT_CONVERGED) return rc;
             k_axpy<<<nb(n), 256, 0, s>>>(x, d, n);
             BEM_LAUNCH_CHECK(c);
-            if ((rc = residual(c, BEM_FP64, c->bvec, x, ri))) return rc;
+            const int rprec = c->prm.residual == BEM_RESIDUAL_DF ? kPrecDF : BEM_FP64;
+            if ((rc = residual(c, rprec, c->bvec, x, ri))) return rc;
             if ((rc = norm2(c, ri, &rnorm))) return rc;
             if (total_iters >= c->prm.max_iters) break;
         }

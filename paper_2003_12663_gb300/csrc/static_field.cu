@@ -72,7 +72,7 @@ extern "C" int bem_eval_field_static(bem_ctx* c, int32_t precision, const double
     // array by an earlier call needs clearing
     int64_t splits = far_splits(c, precision, M);
     splits = std::max<int64_t>(1, std::min<int64_t>(splits, kScratchDoubles / (4 * M)));
-    FarTargets T{nullptr, nullptr, pts, M};
+    FarTargets T{nullptr, nullptr, nullptr, pts, M};
     int rc = launch_far(c, precision, T, u, 1, 0, (int)splits, scratch);
     if (rc) return rc;
     return launch_points_near(c, precision, M, pts, u, scratch, (int)splits, phi, E);

@@ -76,7 +76,7 @@ def test_assemble_row_block(case, bem):
     assert _rel_rows(G, A[r0:r1]) < 1e-11
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-6)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-6), (2, 1e-11)])
 def test_matvec(case, bem, prec, tol):
     name, mesh, ctx, P, A = case
     rng = np.random.default_rng(11)
@@ -101,6 +101,32 @@ def test_solve_matches_lu(case, bem, prec):
         from oracle import oracle as O
         u_exact = P.solve(O.EXACT)
         assert np.linalg.norm(u - u_exact) / np.linalg.norm(u_exact) < 1e-6
+
+
+def test_matvec_df_reproduces_fp64(case, bem):
+    """The double-FP32 pass reproduces the FP64 operator, including the pairs the
+    FP32 and FP64 classifications disagree on."""
+    name, mesh, ctx, P, A = case
+    x = torch.tensor(np.random.default_rng(12).normal(size=ctx.nunk))
+    y64 = ctx.matvec(x, precision=bem.FP64).cpu().numpy()
+    ydf = ctx.matvec(x, precision=bem.DF).cpu().numpy()
+    assert np.abs(ydf - y64).max() / np.abs(y64).max() < 1e-12
+
+
+@pytest.mark.parametrize("residual", [0, 1])
+def test_mixed_solve_residual_modes(case, bem, residual):
+    """BEM_MIXED with the refinement residual in double-FP32 (default) or FP64:
+    the FP64 residual of the result meets the tolerance and sigma matches LU."""
+    name, mesh, ctx, P, A = case
+    c2 = bem.Context(mesh, residual=residual)
+    u, iters, rel = c2.solve(bem.MIXED, tol=1e-10)
+    b = c2.rhs()
+    r = (b[0] - c2.matvec(u[0], precision=bem.FP64)).norm() / b[0].norm()
+    assert r.item() <= 2e-10, (r.item(), rel)
+    u_ref = np.linalg.solve(A, P.rhs())
+    uu = u[0].cpu().numpy()
+    assert np.linalg.norm(uu - u_ref) / np.linalg.norm(u_ref) < 1e-6
+    c2.close()
 
 
 @pytest.mark.parametrize("prec", [0, 1])
