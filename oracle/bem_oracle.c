@@ -319,3 +319,231 @@ void oracle_field(int64_t M, const double* pts, const int64_t* self_idx, int64_t
         E[3 * i + 2] = e[2];
     }
 }
+
+/* ------------------------------------------------------------- field lines */
+/*
+ * Breakdown criterion, Eq. (Breakdowncrit): K = int_gamma alpha_eff(|E|) ds along a
+ * field line gamma, traced from a seed on an electrode.
+ *
+ * The line follows dx/ds = s0 E/|E| (arc length s), s0 = sign(E.n) at the seed with
+ * n the normal of the triangle whose centroid is nearest to the seed, and carries K
+ * as an extra state, dK/ds = alpha_eff(|E(x)|), with
+ *     alpha_eff(E) = c (E - E0)^2  for E > E0,   -d  otherwise.
+ * Classical RK4 with step h advances (x, K).  Because alpha_eff jumps at E = E0, the
+ * integrand branch ("side") is part of the state: inside a step every stage uses the
+ * branch of the current side.  When the end of a step lands on the other side, the
+ * crossing is located on the RK4 step itself, g(sig) = |E(x(sig))| - E0 with x(sig)
+ * the end of an RK4 step of length sig, by the Illinois variant of regula falsi; the
+ * step is split there and the side flips.  Terminal events are located the same way:
+ * |x| = r_max (status 1), entering another electrode (status 2: the solid-angle sum
+ * of that electrode's triangles, sum_j G_j.n_j with unit density, falls below -1/2;
+ * -1 inside a closed body, 0 outside), |E| < e_floor (status 4, at a step start),
+ * max_steps full steps (status 3), a non-finite field at a step start (status -1: the
+ * flat-triangle field is singular on edges and vertices).
+ */
+typedef struct {
+    int analytic;         /* 1: field of a point charge q at the origin, E = q x/|x|^3 */
+    double q;
+    int64_t np;
+    const double* X;
+    const int32_t* tri;
+    const double* geom;
+    const double* u;
+    const int32_t* region;
+    const int32_t* electrode; /* per region: 1 for conductor and floating bodies */
+    double eta;
+    int nu, nv;
+    const double *uk, *wu, *vl, *wv;
+} fsrc;
+
+typedef struct {
+    double h, r_max, c, E0, d, e_floor;
+    int64_t max_steps;
+} tparams;
+
+static void field_pt(const fsrc* F, vec x, int seed_region, vec* E, double* ind)
+{
+    if (F->analytic) {
+        double r = norm(x);
+        *E = scl(x, F->q / (r * r * r));
+        *ind = 0.0;
+        return;
+    }
+    double xp[3] = {x.x, x.y, x.z};
+    vec e = {0.0, 0.0, 0.0};
+    double s_ind = 0.0;
+    for (int64_t j = 0; j < F->np; ++j) {
+        double s, g[3];
+        pair(1, F->eta, xp, 0, F->X, F->tri + 3 * j, F->geom + 11 * j, F->nu, F->uk, F->wu, F->nv,
+             F->vl, F->wv, &s, g);
+        e.x += F->u[j] * g[0];
+        e.y += F->u[j] * g[1];
+        e.z += F->u[j] * g[2];
+        int rj = F->region[j];
+        if (rj != seed_region && F->electrode[rj]) {
+            const double* n = F->geom + 11 * j;
+            s_ind += g[0] * n[0] + g[1] * n[1] + g[2] * n[2];
+        }
+    }
+    *E = e;
+    *ind = s_ind;
+}
+
+static double alpha_eff(const tparams* P, double Em, int side)
+{
+    return side > 0 ? P->c * (Em - P->E0) * (Em - P->E0) : -P->d;
+}
+
+/* one RK4 step of length s from (x, K) on branch side; returns the end state */
+static void rk4_step(const fsrc* F, const tparams* P, int seed_region, double s0, int side, vec x,
+                     double K, double s, vec* x1, double* K1)
+{
+    vec k[4];
+    double a[4];
+    vec y = x;
+    for (int st = 0; st < 4; ++st) {
+        vec E;
+        double ind;
+        field_pt(F, y, seed_region, &E, &ind);
+        double Em = norm(E);
+        k[st] = scl(E, s0 / Em);
+        a[st] = alpha_eff(P, Em, side);
+        if (st < 3) y = add(x, scl(k[st], st < 2 ? 0.5 * s : s));
+    }
+    *x1 = add(x, scl(add(add(k[0], scl(add(k[1], k[2]), 2.0)), k[3]), s / 6.0));
+    *K1 = K + s / 6.0 * (a[0] + 2.0 * (a[1] + a[2]) + a[3]);
+}
+
+enum { EV_ALPHA = 0, EV_RMAX = 1, EV_ELECTRODE = 2 };
+
+/* event function of kind ev at the end of an RK4 step of length sig */
+static double event_g(const fsrc* F, const tparams* P, int seed_region, double s0, int side, vec x,
+                      double K, double sig, int ev)
+{
+    vec x1, E;
+    double K1, ind;
+    rk4_step(F, P, seed_region, s0, side, x, K, sig, &x1, &K1);
+    if (ev == EV_RMAX) return norm(x1) - P->r_max;
+    field_pt(F, x1, seed_region, &E, &ind);
+    if (ev == EV_ALPHA) return norm(E) - P->E0;
+    return ind + 0.5;
+}
+
+/* Illinois regula falsi on [0, b] where g(0) = ga and g(b) = gb differ in sign */
+static double illinois(const fsrc* F, const tparams* P, int seed_region, double s0, int side, vec x,
+                       double K, double b, double ga, double gb, int ev)
+{
+    double a = 0.0, c = b;
+    int last = 0;
+    for (int it = 0; it < 100; ++it) {
+        c = (ga * b - gb * a) / (ga - gb);
+        double gc = event_g(F, P, seed_region, s0, side, x, K, c, ev);
+        if (gc == 0.0) break;
+        if ((gc > 0.0) == (gb > 0.0)) {
+            b = c; gb = gc;
+            if (last == -1) ga *= 0.5;
+            last = -1;
+        } else {
+            a = c; ga = gc;
+            if (last == 1) gb *= 0.5;
+            last = 1;
+        }
+        if (b - a <= 1e-14 * P->h) break;
+    }
+    return c;
+}
+
+static void trace_one(const fsrc* F, const tparams* P, const double* seed, double* K_out,
+                      int32_t* status, int32_t* nsteps, double* xend)
+{
+    vec x = mk(seed);
+    double K = 0.0;
+    int seed_region = -1;
+    double s0 = 1.0;
+    vec E;
+    double ind;
+    field_pt(F, x, -2, &E, &ind);
+    if (!F->analytic) {
+        int64_t best = 0;
+        double bd = 1e300;
+        for (int64_t j = 0; j < F->np; ++j) {
+            const double* c = F->geom + 11 * j + 4;
+            double dd = (x.x - c[0]) * (x.x - c[0]) + (x.y - c[1]) * (x.y - c[1]) + (x.z - c[2]) * (x.z - c[2]);
+            if (dd < bd) { bd = dd; best = j; }
+        }
+        seed_region = F->region[best];
+        const double* n = F->geom + 11 * best;
+        s0 = (E.x * n[0] + E.y * n[1] + E.z * n[2]) >= 0.0 ? 1.0 : -1.0;
+    } else {
+        s0 = (dot(E, x) >= 0.0) ? 1.0 : -1.0;
+    }
+    int side = norm(E) > P->E0 ? 1 : -1;
+    int st = 3;
+    int64_t step = 0;
+    for (; step < P->max_steps; ++step) {
+        field_pt(F, x, seed_region, &E, &ind);
+        if (!isfinite(norm(E))) { st = -1; break; }  /* on an edge or vertex: singular field */
+        if (norm(E) < P->e_floor) { st = 4; break; }
+        double rem = P->h;
+        int done = 0;
+        for (int nev = 0; rem > 0.0 && nev < 4; ++nev) {
+            vec x1;
+            double K1;
+            rk4_step(F, P, seed_region, s0, side, x, K, rem, &x1, &K1);
+            vec E1;
+            double ind1;
+            field_pt(F, x1, seed_region, &E1, &ind1);
+            double best = 2.0 * rem;
+            int which = -1;
+            if ((norm(E1) > P->E0) != (side > 0)) {
+                double ga = event_g(F, P, seed_region, s0, side, x, K, 0.0, EV_ALPHA);
+                double sg = illinois(F, P, seed_region, s0, side, x, K, rem, ga, norm(E1) - P->E0, EV_ALPHA);
+                if (sg < best) { best = sg; which = EV_ALPHA; }
+            }
+            if (norm(x1) >= P->r_max) {
+                double sg = illinois(F, P, seed_region, s0, side, x, K, rem, norm(x) - P->r_max,
+                                     norm(x1) - P->r_max, EV_RMAX);
+                if (sg < best) { best = sg; which = EV_RMAX; }
+            }
+            if (ind1 < -0.5) {
+                double ga = event_g(F, P, seed_region, s0, side, x, K, 0.0, EV_ELECTRODE);
+                double sg = illinois(F, P, seed_region, s0, side, x, K, rem, ga, ind1 + 0.5, EV_ELECTRODE);
+                if (sg < best) { best = sg; which = EV_ELECTRODE; }
+            }
+            if (which < 0) {
+                x = x1; K = K1; rem = 0.0;
+                break;
+            }
+            rk4_step(F, P, seed_region, s0, side, x, K, best, &x, &K);
+            if (which == EV_ALPHA) {
+                side = -side;
+                rem -= best;
+                continue;
+            }
+            st = which == EV_RMAX ? 1 : 2;
+            done = 1;
+            break;
+        }
+        if (done) break;
+    }
+    *K_out = K;
+    *status = st;
+    *nsteps = (int32_t)step;
+    xend[0] = x.x; xend[1] = x.y; xend[2] = x.z;
+}
+
+/* L field lines from seeds[L][3].  analytic != 0: point-charge field of strength q
+ * (mesh arguments unused).  electrode[nregions]: 1 for conductor/floating regions. */
+void oracle_trace(int64_t L, const double* seeds, int analytic, double q, int64_t np,
+                  const double* X, const int32_t* tri, const double* geom, const double* u,
+                  const int32_t* region, const int32_t* electrode, double eta, int nu,
+                  const double* uk, const double* wu, int nv, const double* vl, const double* wv,
+                  double h, double r_max, double c, double E0, double d, double e_floor,
+                  int64_t max_steps, double* K, int32_t* status, int32_t* nsteps, double* xend)
+{
+    fsrc F = {analytic, q, np, X, tri, geom, u, region, electrode, eta, nu, nv, uk, wu, vl, wv};
+    tparams P = {h, r_max, c, E0, d, e_floor, max_steps};
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t l = 0; l < L; ++l)
+        trace_one(&F, &P, seeds + 3 * l, K + l, status + l, nsteps + l, xend + 3 * l);
+}

@@ -60,8 +60,62 @@ def lib():
         L.oracle_field.argtypes = [_i64, _dp, _lp, _i64, _dp, _ip, _dp, _dp, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp,
                                    _dp, _dp, _dp]
+        L.oracle_trace.argtypes = [_i64, _dp, ctypes.c_int, ctypes.c_double, _i64, _dp, _ip, _dp,
+                                   _dp, _ip, _ip, ctypes.c_double, ctypes.c_int, _dp, _dp,
+                                   ctypes.c_int, _dp, _dp] + [ctypes.c_double] * 6 + \
+                                  [_i64, _dp, _ip, _ip, _dp]
         _lib = L
     return _lib
+
+
+class TraceParams:
+    """Field-line tracing parameters (Eq. Breakdowncrit): RK4 step h in arc length,
+    stop radius r_max, alpha_eff(E) = c (E - E0)^2 for E > E0 else -d, stop when
+    |E| < e_floor or after max_steps steps."""
+
+    def __init__(self, h=1e-3, r_max=10.0, c=1e-2, E0=0.5, d=0.1, e_floor=1e-12, max_steps=200000):
+        self.h, self.r_max, self.c, self.E0, self.d = h, r_max, c, E0, d
+        self.e_floor, self.max_steps = e_floor, max_steps
+
+    def args(self):
+        return [self.h, self.r_max, self.c, self.E0, self.d, self.e_floor, int(self.max_steps)]
+
+
+def _trace_call(L, seeds, analytic, q, P, u, tp):
+    seeds = _c(seeds, np.float64).reshape(-1, 3)
+    K = np.zeros(L)
+    st = np.zeros(L, np.int32)
+    ns = np.zeros(L, np.int32)
+    xe = np.zeros((L, 3))
+    if P is None:
+        dummy_d = np.zeros(16)
+        dummy_i = np.zeros(16, np.int32)
+        mesh_args = [0, _d(dummy_d), dummy_i.ctypes.data_as(_ip), _d(dummy_d), _d(dummy_d),
+                     dummy_i.ctypes.data_as(_ip), dummy_i.ctypes.data_as(_ip), 4.0, 1, _d(dummy_d),
+                     _d(dummy_d), 1, _d(dummy_d), _d(dummy_d)]
+        keep = (dummy_d, dummy_i)
+    else:
+        uu = _c(u[: P.N], np.float64)
+        reg = _c(P.mesh.region, np.int32)
+        elec = np.array([1 if r["kind"] in ("conductor", "floating") else 0 for r in P.mesh.regions],
+                        np.int32)
+        ru, rwu, rv, rwv = P.rule
+        mesh_args = [P.N, _d(P.X), P.tri.ctypes.data_as(_ip), _d(P.geom), _d(uu),
+                     reg.ctypes.data_as(_ip), elec.ctypes.data_as(_ip), P.eta, len(ru), _d(ru),
+                     _d(rwu), len(rv), _d(rv), _d(rwv)]
+        keep = (uu, reg, elec)
+    lib().oracle_trace(L, _d(seeds), int(analytic), float(q), *mesh_args, *tp.args(), _d(K),
+                       st.ctypes.data_as(_ip), ns.ctypes.data_as(_ip), _d(xe))
+    del keep
+    return K, st, ns, xe
+
+
+def trace_point_charge(seeds, q=1.0, tp=None):
+    """Field lines of E = q x / |x|^3 (the continuum field of a unit sphere at
+    potential q), for pinning the integrator and its event handling."""
+    tp = tp or TraceParams()
+    seeds = np.asarray(seeds, np.float64).reshape(-1, 3)
+    return _trace_call(len(seeds), seeds, 1, q, None, None, tp)
 
 
 def _d(a):
@@ -250,3 +304,10 @@ class Problem:
         """E on the + side at every centroid: E_PV(c_i) + u_i n_i / 2."""
         _, E = self.field(u_sigma, self.centroids, np.arange(self.N), mode)
         return E + 0.5 * u_sigma[: self.N, None] * self.normals
+
+    def trace(self, u_sigma, seeds, tp=None):
+        """Field lines and K = int alpha_eff(|E|) ds (Eq. Breakdowncrit) in the field
+        of sigma (the method's pair integrals).  Returns K, status, nsteps, xend."""
+        tp = tp or TraceParams()
+        seeds = np.asarray(seeds, np.float64).reshape(-1, 3)
+        return _trace_call(len(seeds), seeds, 0, 0.0, self, u_sigma, tp)
