@@ -231,6 +231,39 @@ int bem_eval_field(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t
 int bem_eval_field_static(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t M,
                           const double* pts_dev, double* phi_dev, double* E_dev);
 
+/* Field-line tracing parameters (Eq. Breakdowncrit). */
+typedef struct {
+    double h;            /* RK4 step in arc length; default 1e-3 */
+    double r_max;        /* stop where |x| = r_max; default 10 */
+    double c, E0, d;     /* alpha_eff(E) = c (E - E0)^2 for E > E0, else -d; 1e-2, 0.5, 0.1 */
+    double e_floor;      /* stop at a step start where |E| < e_floor; default 1e-12 */
+    int64_t max_steps;   /* stop after this many steps; default 200000 */
+} bem_trace_params;
+
+void bem_default_trace_params(bem_trace_params* tp);
+
+/*
+ * Breakdown integral along field lines (Sec. 1, Eq. Breakdowncrit):
+ *   K = int_gamma alpha_eff(|E|) ds,
+ * gamma the field line through each seed, dx/ds = s0 E/|E|, s0 = sign(E.n) at the
+ * seed (n: normal of the triangle whose centroid is nearest to the seed, so lines
+ * leave the electrode), E the field of u (as bem_eval_field).  Classical RK4 with
+ * step h on (x, K).  The branch of alpha_eff is part of the state; where a step
+ * ends on the other side of |E| = E0 the crossing is located on the re-stepped RK4
+ * step (Illinois regula falsi) and the step is split there, so K is a smooth
+ * function of the data.  Stops, located the same way: |x| = r_max (status 1);
+ * entering another conductor or floating body (status 2: the solid angle of its
+ * triangles passes 2 pi).  At step starts: |E| < e_floor (status 4), non-finite
+ * field (status -1: seed on an edge or vertex); max_steps steps: status 3.
+ * u_dev: device double [>= N]; seeds_dev: device double [L][3]; tp: host, NULL =
+ * defaults; outputs (device): K_dev double [L], status_dev int32 [L], nsteps_dev
+ * int32 [L] (completed steps), xend_dev double [L][3] (end point), any may be NULL.
+ * One CTA per line; precision BEM_FP64 or BEM_MIXED (regular pairs in FP32).
+ */
+int bem_trace_lines(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t L,
+                    const double* seeds_dev, const bem_trace_params* tp, double* K_dev,
+                    int32_t* status_dev, int32_t* nsteps_dev, double* xend_dev);
+
 /*
  * Field on the + side of the surface at every centroid ("E surface" of Sec. 5):
  *   E+(c_i) = E_PV(c_i) + u_i n_i / 2   (Eq. ADL read as E+.n = sigma/2 + K' sigma).

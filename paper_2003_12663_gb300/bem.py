@@ -53,6 +53,12 @@ class bem_params(ctypes.Structure):
 RESIDUAL_DF, RESIDUAL_FP64 = 0, 1
 
 
+class bem_trace_params(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("r_max", ctypes.c_double), ("c", ctypes.c_double),
+                ("E0", ctypes.c_double), ("d", ctypes.c_double), ("e_floor", ctypes.c_double),
+                ("max_steps", ctypes.c_int64)]
+
+
 class bem_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("far_launches", ctypes.c_int64 * 3),
                 ("pairs", ctypes.c_int64 * 3), ("near_pairs", ctypes.c_int64 * 3),
@@ -86,6 +92,9 @@ _SIGS = {
     "bem_eval_field": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp]),
     "bem_eval_field_static": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp]),
     "bem_surface_field": (_i32, [_vp, _i32, _vp, _vp]),
+    "bem_default_trace_params": (None, [ctypes.POINTER(bem_trace_params)]),
+    "bem_trace_lines": (_i32, [_vp, _i32, _vp, _i64, _vp, ctypes.POINTER(bem_trace_params), _vp,
+                               _vp, _vp, _vp]),
 }
 _lib = None
 
@@ -245,6 +254,26 @@ class Context:
         _check(lib().bem_eval_field_static(self.h, precision, _ptr(u), M, _ptr(pts), _ptr(phi),
                                            _ptr(E)), self.h)
         return phi, E
+
+    def trace_lines(self, u, seeds, precision=FP64, **tp):
+        """bem_trace_lines: K, status, nsteps, xend per seed (device tensors)."""
+        t = self._torch
+        p = bem_trace_params()
+        lib().bem_default_trace_params(ctypes.byref(p))
+        for k, v in tp.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        u = self._dev(u)
+        seeds = self._dev(seeds)
+        L = seeds.shape[0]
+        K = t.empty(L, dtype=t.float64, device="cuda")
+        st = t.empty(L, dtype=t.int32, device="cuda")
+        ns = t.empty(L, dtype=t.int32, device="cuda")
+        xe = t.empty((L, 3), dtype=t.float64, device="cuda")
+        _check(lib().bem_trace_lines(self.h, precision, _ptr(u), L, _ptr(seeds), ctypes.byref(p),
+                                     _ptr(K), _ptr(st), _ptr(ns), _ptr(xe)), self.h)
+        return K, st, ns, xe
 
     def surface_field(self, u, precision=FP64):
         t = self._torch

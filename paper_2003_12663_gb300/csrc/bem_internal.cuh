@@ -60,6 +60,8 @@ struct bem_ctx {
     double* row_b = nullptr;       // [np] dielectric: eps+ - eps-
     double* row_w = nullptr;       // [np] floating: A_i eps+ / area_f
     double* region_V0 = nullptr;   // [nregions]
+    int32_t* d_region = nullptr;   // [np] region of every triangle
+    int32_t* d_electrode = nullptr;  // [nregions] 1 for conductor and floating regions
     int32_t* float_rows = nullptr; // rows of every floating body, grouped
     int32_t* float_off = nullptr;  // [nfloat+1]
     double* jinv = nullptr;        // [nunk] inverse Jacobi diagonal

@@ -346,7 +346,8 @@ static void free_ctx(bem_ctx* c)
                     c->float_rows, c->float_off, c->jinv, c->near_ptr, c->near_col, c->near_val,
                     c->near_flag, c->part, c->field, c->neut, c->pts_stage, c->V, c->wvec,
                     c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
-                    c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df};
+                    c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df, c->d_region,
+                    c->d_electrode};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hcol_host) cudaFreeHost(c->hcol_host);
@@ -603,6 +604,15 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->row_b, rb.data(), np * 8, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->row_w, rw.data(), np * 8, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->region_V0, V0.data(), nreg * 8, cudaMemcpyHostToDevice, s));
+    {
+        std::vector<int32_t> elec(nreg);
+        for (int r = 0; r < nreg; ++r)
+            elec[r] = (c->regions[r].kind == BEM_CONDUCTOR || c->regions[r].kind == BEM_FLOATING) ? 1 : 0;
+        if ((rc = dalloc(c, &c->d_region, np)) || (rc = dalloc(c, &c->d_electrode, nreg))) return rc;
+        BEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_region, c->h_region.data(), np * 4, cudaMemcpyHostToDevice, s));
+        BEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_electrode, elec.data(), nreg * 4, cudaMemcpyHostToDevice, s));
+        BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    }
     if (!fr.empty())
         BEM_CUDA_TRY(c, cudaMemcpyAsync(c->float_rows, fr.data(), fr.size() * 4, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->float_off, fo.data(), fo.size() * 4, cudaMemcpyHostToDevice, s));
