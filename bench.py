@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--far32-variant", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="FP32 regular-pair kernel variant (0: tuned at context creation)")
     ap.add_argument("--mode", default="step", choices=["step", "matvec"],
                     help="matvec: only W+K mixed matvecs of the workload (a small case for ncu)")
     return ap.parse_args()
@@ -62,7 +64,7 @@ def run_matvec(args):
     __graft_entry__.build()
     from paper_2003_12663_gb300 import bem
     mesh, _ = workload(args)
-    ctx = bem.Context(mesh)
+    ctx = bem.Context(mesh, far32_variant=args.far32_variant)
     x = torch.randn(ctx.nunk, dtype=torch.float64, device="cuda", generator=None)
     for _ in range(args.warmup + args.steps):
         ctx.matvec(x, bem.MIXED)
@@ -194,8 +196,8 @@ def committed_traffic():
         return None
     vals = {}
     for line in open(p):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
     if vals.get("far.cu sha256[:16]") != far_kernel_hash():
         return None
@@ -247,7 +249,7 @@ def run_ours(args):
 
     mesh, pts = workload(args)
     dev = torch.device("cuda", local)
-    ctx = bem.Context(mesh, timing=1)
+    ctx = bem.Context(mesh, timing=1, far32_variant=args.far32_variant)
     Q = ctx.params.far_order ** 2
     pts_d = torch.tensor(pts, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -297,7 +299,9 @@ def run_ours(args):
     traffic = committed_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "kernel": "k_far32 (FP32 regular pairs, phi+E)",
+                "kernel": ("k_far32 (scalar)" if cnt["far32_variant"] == 1 else
+                           f"k_far32p (packed f32x2, {cnt['far32_variant']} target pairs/thread)")
+                          + ": FP32 regular pairs, phi+E",
                 "peak_basis": f"derived FP32 peak: {props.multi_processor_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz",
                 "flops_per_launch": flops / n_launch, "avg_launch_ms": far_ms / n_launch,
                 "fp64_far_ms_per_step": cnt["far_ms"][0] / args.steps,

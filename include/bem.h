@@ -92,6 +92,10 @@ typedef struct {
     int32_t timing;          /* != 0: time every regular-pair kernel with CUDA events (bem_counters) */
     int32_t residual;        /* BEM_MIXED refinement residual b - A u: BEM_RESIDUAL_DF (default)
                                 or BEM_RESIDUAL_FP64 */
+    int32_t far32_variant;   /* FP32 regular-pair kernel: 1 scalar, 2 or 4 packed target pairs
+                                per thread; 0 (default): bem_create times the candidates on the
+                                mesh's own matvec and keeps the fastest (N >= 4096; else 2) */
+    int32_t reserved;
 } bem_params;
 
 /* How the iterative refinement of BEM_MIXED forms its residual b - A u.
@@ -111,6 +115,7 @@ typedef struct {
     double far_ms[3];           /* summed regular-pair kernel time in ms (params.timing != 0) */
     int64_t matvecs[3];         /* matrix-free products, solver-internal ones included */
     int64_t gmres_iters;        /* Arnoldi steps */
+    int64_t far32_variant;      /* FP32 kernel variant in use (1, 2 or 4; not reset) */
 } bem_counters;
 
 typedef struct bem_ctx bem_ctx;

@@ -47,7 +47,8 @@ class bem_params(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("far_order", ctypes.c_int32),
                 ("gmres_restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("max_points", ctypes.c_int64),
-                ("timing", ctypes.c_int32), ("residual", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("residual", ctypes.c_int32),
+                ("far32_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 RESIDUAL_DF, RESIDUAL_FP64 = 0, 1
@@ -63,7 +64,7 @@ class bem_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("far_launches", ctypes.c_int64 * 3),
                 ("pairs", ctypes.c_int64 * 3), ("near_pairs", ctypes.c_int64 * 3),
                 ("far_ms", ctypes.c_double * 3), ("matvecs", ctypes.c_int64 * 3),
-                ("gmres_iters", ctypes.c_int64)]
+                ("gmres_iters", ctypes.c_int64), ("far32_variant", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

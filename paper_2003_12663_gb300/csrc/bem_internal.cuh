@@ -49,6 +49,9 @@ struct bem_ctx {
     float4* node32 = nullptr;   // [np][Q] (y, w)          FP32
     double4* node64 = nullptr;  // [np][Q] (y, w)          FP64
     float4* node_lo32 = nullptr;  // [np][Q] node - node32 (low parts of the double-FP32 nodes)
+    float4* qnode = nullptr;      // [np][Q] FP32 nodes with sigma folded into w (per call)
+    float4* chunk_sph = nullptr;  // [np/32 rounded up] bounding sphere of 32 triangles' near zones
+    int far32_tp = 2;             // FP32 kernel variant: 1 scalar, 2 or 4 packed target pairs
     float4* tgt_lo32 = nullptr;   // [np] centroid - tgt32
     float4* tgt32 = nullptr;    // [np] centroids          FP32
     double4* tgt64 = nullptr;   // [np] centroids          FP64

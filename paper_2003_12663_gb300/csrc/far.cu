@@ -135,6 +135,213 @@ k_far32(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_t
     }
 }
 
+// ---------------------------------------------------------------- packed FP32
+// The same regular-pair sums with Blackwell's paired FP32 instructions
+// (add/mul/fma on float2): every thread holds 2*TP targets as TP pairs, so one
+// instruction advances two pair-ops and the FP32 units, not instruction issue,
+// set the pace.  The node stream arrives with sigma folded into the weights
+// (k_prescale) and already duplicated into pairs (-y, -y, w) in shared memory.
+// Before each chunk of PC triangles the CTA compares the bounding sphere of its
+// targets with the chunk's precomputed sphere (circumcentres + eta R, with a
+// rounding margin): if every pair is certainly regular, the chunk runs as a flat
+// node stream without any per-triangle classification ("fast"); otherwise each
+// triangle's sums are masked per target by is_far32, exactly like k_far32.
+__global__ void k_prescale(int64_t n, int Q, const float4* __restrict__ node,
+                           const double* __restrict__ u, float4* __restrict__ qnode)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 v = node[i];
+    v.w = v.w * __double2float_rn(u[i / Q]);
+    qnode[i] = v;
+}
+
+template <int TP, int Q, bool RAW>
+__global__ void __launch_bounds__(kThreads)
+k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_t M,
+         const float4* __restrict__ hdr, const float4* __restrict__ qnode,
+         const float4* __restrict__ chunk_sph, int64_t np, int64_t per_split,
+         double* __restrict__ part)
+{
+    constexpr int PC = kPC32;
+    constexpr int TR = 2 * TP;
+    __shared__ float4 s_hdr[PC];
+    __shared__ float4 s_n2[PC * Q][2];   // (-x,-x,-y,-y), (-z,-z,w,w)
+    __shared__ float s_box[6][kThreads / 32];
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * TR);
+    const int split = blockIdx.y;
+    const int64_t p0 = (int64_t)split * per_split;
+    const int64_t p1 = min(np, p0 + per_split);
+
+    float2 tx[TP], ty[TP], tz[TP];
+    float bmin[3] = {3e38f, 3e38f, 3e38f}, bmax[3] = {-3e38f, -3e38f, -3e38f};
+#pragma unroll
+    for (int q = 0; q < TP; ++q) {
+        float v[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t t = min(base + (2 * q + h) * kThreads + tid, M - 1);
+            if (RAW) {
+                v[h][0] = __double2float_rn(tpts[3 * t]);
+                v[h][1] = __double2float_rn(tpts[3 * t + 1]);
+                v[h][2] = __double2float_rn(tpts[3 * t + 2]);
+            } else {
+                const float4 a = t32[t];
+                v[h][0] = a.x; v[h][1] = a.y; v[h][2] = a.z;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                bmin[c] = fminf(bmin[c], v[h][c]);
+                bmax[c] = fmaxf(bmax[c], v[h][c]);
+            }
+        }
+        tx[q] = make_float2(v[0][0], v[1][0]);
+        ty[q] = make_float2(v[0][1], v[1][1]);
+        tz[q] = make_float2(v[0][2], v[1][2]);
+    }
+    // bounding box of the CTA's targets -> centre and radius (uniform)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            bmin[c] = fminf(bmin[c], __shfl_xor_sync(0xffffffffu, bmin[c], o));
+            bmax[c] = fmaxf(bmax[c], __shfl_xor_sync(0xffffffffu, bmax[c], o));
+        }
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            s_box[c][tid >> 5] = bmin[c];
+            s_box[3 + c][tid >> 5] = bmax[c];
+        }
+    __syncthreads();
+    float tc[3], tr = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float lo = s_box[c][0], hi = s_box[3 + c][0];
+#pragma unroll
+        for (int w = 1; w < kThreads / 32; ++w) {
+            lo = fminf(lo, s_box[c][w]);
+            hi = fmaxf(hi, s_box[3 + c][w]);
+        }
+        tc[c] = 0.5f * (lo + hi);
+        tr += (hi - lo) * (hi - lo);
+    }
+    tr = 0.5f * sqrtf(tr) * 1.0001f + 1e-6f;
+
+    float2 acc[TP][4], cmp[TP][4];
+#pragma unroll
+    for (int q = 0; q < TP; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[q][c] = cmp[q][c] = make_float2(0.f, 0.f);
+    const float2 eps2 = make_float2(1e-20f, 1e-20f);
+
+    for (int64_t c0 = p0; c0 < p1; c0 += PC) {
+        const int npc = (int)min((int64_t)PC, p1 - c0);
+        __syncthreads();
+        for (int k = tid; k < npc; k += kThreads) s_hdr[k] = hdr[c0 + k];
+        for (int k = tid; k < npc * Q; k += kThreads) {
+            const float4 v = qnode[c0 * Q + k];
+            s_n2[k][0] = make_float4(-v.x, -v.x, -v.y, -v.y);
+            s_n2[k][1] = make_float4(-v.z, -v.z, v.w, v.w);
+        }
+        __syncthreads();
+        const float4 cs = chunk_sph[c0 / PC];
+        const float ddx = cs.x - tc[0], ddy = cs.y - tc[1], ddz = cs.z - tc[2];
+        const bool fast = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz) > tr + cs.w;
+        float2 cp[TP][4];
+#pragma unroll
+        for (int q = 0; q < TP; ++q)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cp[q][c] = make_float2(0.f, 0.f);
+        if (fast) {
+            for (int p = 0; p < npc; ++p) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    const float4 a = s_n2[p * Q + k][0], b = s_n2[p * Q + k][1];
+                    const float2 mx = make_float2(a.x, a.y), my = make_float2(a.z, a.w);
+                    const float2 mz = make_float2(b.x, b.y), w2 = make_float2(b.z, b.w);
+#pragma unroll
+                    for (int q = 0; q < TP; ++q) {
+                        const float2 dx = __fadd2_rn(tx[q], mx), dy = __fadd2_rn(ty[q], my),
+                                     dz = __fadd2_rn(tz[q], mz);
+                        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+                        const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                        const float2 t = __fmul2_rn(w2, ri);
+                        const float2 t3 = __fmul2_rn(t, __fmul2_rn(ri, ri));
+                        cp[q][0] = __fadd2_rn(cp[q][0], t);
+                        cp[q][1] = __ffma2_rn(t3, dx, cp[q][1]);
+                        cp[q][2] = __ffma2_rn(t3, dy, cp[q][2]);
+                        cp[q][3] = __ffma2_rn(t3, dz, cp[q][3]);
+                    }
+                }
+            }
+        } else {
+            for (int p = 0; p < npc; ++p) {
+                float2 ps[TP], gx[TP], gy[TP], gz[TP];
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    const float4 a = s_n2[p * Q + k][0], b = s_n2[p * Q + k][1];
+                    const float2 mx = make_float2(a.x, a.y), my = make_float2(a.z, a.w);
+                    const float2 mz = make_float2(b.x, b.y), w2 = make_float2(b.z, b.w);
+#pragma unroll
+                    for (int q = 0; q < TP; ++q) {
+                        const float2 dx = __fadd2_rn(tx[q], mx), dy = __fadd2_rn(ty[q], my),
+                                     dz = __fadd2_rn(tz[q], mz);
+                        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+                        const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                        const float2 t = __fmul2_rn(w2, ri);
+                        const float2 t3 = __fmul2_rn(t, __fmul2_rn(ri, ri));
+                        if (k == 0) {
+                            ps[q] = t;
+                            gx[q] = __fmul2_rn(t3, dx); gy[q] = __fmul2_rn(t3, dy); gz[q] = __fmul2_rn(t3, dz);
+                        } else {
+                            ps[q] = __fadd2_rn(ps[q], t);
+                            gx[q] = __ffma2_rn(t3, dx, gx[q]);
+                            gy[q] = __ffma2_rn(t3, dy, gy[q]);
+                            gz[q] = __ffma2_rn(t3, dz, gz[q]);
+                        }
+                    }
+                }
+                const float4 h = s_hdr[p];
+#pragma unroll
+                for (int q = 0; q < TP; ++q) {
+                    const bool f0 = is_far32(tx[q].x, ty[q].x, tz[q].x, h);
+                    const bool f1 = is_far32(tx[q].y, ty[q].y, tz[q].y, h);
+                    cp[q][0] = __fadd2_rn(cp[q][0], make_float2(f0 ? ps[q].x : 0.f, f1 ? ps[q].y : 0.f));
+                    cp[q][1] = __fadd2_rn(cp[q][1], make_float2(f0 ? gx[q].x : 0.f, f1 ? gx[q].y : 0.f));
+                    cp[q][2] = __fadd2_rn(cp[q][2], make_float2(f0 ? gy[q].x : 0.f, f1 ? gy[q].y : 0.f));
+                    cp[q][3] = __fadd2_rn(cp[q][3], make_float2(f0 ? gz[q].x : 0.f, f1 ? gz[q].y : 0.f));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < TP; ++q)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {  // Kahan: acc + cmp carries the running sum
+                const float2 y = __fadd2_rn(cp[q][c], make_float2(-cmp[q][c].x, -cmp[q][c].y));
+                const float2 t = __fadd2_rn(acc[q][c], y);
+                const float2 dd = __fadd2_rn(t, make_float2(-acc[q][c].x, -acc[q][c].y));
+                cmp[q][c] = __fadd2_rn(dd, make_float2(-y.x, -y.y));
+                acc[q][c] = t;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < TP; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t t = base + (2 * q + h) * kThreads + tid;
+            if (t < M) {
+                double* o = part + ((int64_t)split * M + t) * 4;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float a = h ? acc[q][c].y : acc[q][c].x, m = h ? cmp[q][c].y : cmp[q][c].x;
+                    o[c] = (double)a - (double)m;
+                }
+            }
+        }
+}
+
 template <int TR, int Q, bool RAW>
 __global__ void __launch_bounds__(kThreads)
 k_far64(const double4* __restrict__ t64, const double* __restrict__ tpts, int64_t M,
@@ -385,9 +592,29 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
              double* part)
 {
     const int64_t np = ctx->np;
-    const int64_t per_split = (np + splits - 1) / splits;
+    // slices start on whole 32-triangle chunks (the chunk spheres of k_far32p)
+    const int64_t per_split = ((np + splits - 1) / splits + kPC32 - 1) / kPC32 * kPC32;
     const bool raw = (T.tpts != nullptr);
-    if (precision == kPrecDF) {
+    if (precision == BEM_MIXED && ctx->far32_tp > 1) {
+        const int64_t n = np * Q;
+        k_prescale<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, Q, ctx->node32, u, ctx->qnode);
+        BEM_LAUNCH_CHECK(ctx);
+        const int tr = 2 * ctx->far32_tp;
+        dim3 grid((unsigned)((T.M + kThreads * tr - 1) / (kThreads * tr)), (unsigned)splits);
+#define FAR32P(TP)                                                                                \
+    if (raw)                                                                                      \
+        k_far32p<TP, Q, true><<<grid, kThreads, 0, ctx->stream>>>(                                \
+            nullptr, T.tpts, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part);   \
+    else                                                                                          \
+        k_far32p<TP, Q, false><<<grid, kThreads, 0, ctx->stream>>>(                               \
+            T.t32, nullptr, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part)
+        if (ctx->far32_tp == 4) {
+            FAR32P(4);
+        } else {
+            FAR32P(2);
+        }
+#undef FAR32P
+    } else if (precision == kPrecDF) {
         if (raw || !T.t32lo) return set_err(ctx, BEM_ERR_ARG, "double-FP32 pass needs centroid targets");
         dim3 grid((unsigned)((T.M + kThreads * kTRdf - 1) / (kThreads * kTRdf)), (unsigned)splits);
         k_far_df<kTRdf, Q><<<grid, kThreads, 0, ctx->stream>>>(
@@ -419,7 +646,8 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
 // four, but no slice shorter than two staging chunks.
 int far_splits(const bem_ctx* ctx, int precision, int64_t M)
 {
-    const int tr = precision == BEM_MIXED ? kTR32 : (precision == kPrecDF ? kTRdf : kTR64);
+    const int tr = precision == BEM_MIXED ? (ctx->far32_tp > 1 ? 2 * ctx->far32_tp : kTR32)
+                                          : (precision == kPrecDF ? kTRdf : kTR64);
     const int pc = precision == BEM_MIXED ? kPC32 : kPC64;
     const int64_t tiles = (M + kThreads * tr - 1) / (kThreads * tr);
     const int64_t slots = (int64_t)std::max(ctx->num_sms, 1) * 4;

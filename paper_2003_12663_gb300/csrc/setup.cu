@@ -228,6 +228,34 @@ __global__ void k_panels(int64_t np, int g, double eta, const double* __restrict
     }
 }
 
+// Bounding sphere of the near zones |x - cc_j| <= eta R_j of 32 consecutive
+// triangles, enlarged by a margin that covers the FP32 rounding of the
+// classification: a target farther than the radius from the centre is regular
+// for all 32 triangles in every kernel of the FP32 form.
+__global__ void k_chunk_spheres(int64_t np, const double* __restrict__ geo, float4* __restrict__ sph)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t j0 = c * 32, j1 = min(np, j0 + 32);
+    if (j0 >= np) return;
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    for (int64_t j = j0; j < j1; ++j) {
+        const double* g = geo + GEO_STRIDE * j;
+        cx += g[GEO_CC]; cy += g[GEO_CC + 1]; cz += g[GEO_CC + 2];
+    }
+    const double inv = 1.0 / (double)(j1 - j0);
+    cx *= inv; cy *= inv; cz *= inv;
+    double r = 0.0;
+    for (int64_t j = j0; j < j1; ++j) {
+        const double* g = geo + GEO_STRIDE * j;
+        const double dx = g[GEO_CC] - cx, dy = g[GEO_CC + 1] - cy, dz = g[GEO_CC + 2] - cz;
+        r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz) + g[GEO_ETAR]);
+    }
+    const double mag = fmax(fabs(cx), fmax(fabs(cy), fabs(cz)));
+    r += 1e-5 * (r + mag) + 1e-30;
+    sph[c] = make_float4(__double2float_rn(cx), __double2float_rn(cy), __double2float_rn(cz),
+                         __double2float_ru(r));
+}
+
 // One warp per collocation row: count (phase 0) or list (phase 1) the triangles
 // that are near in the FP32 or the FP64 classification.  Columns ascend.
 __global__ void k_near_rows(int64_t np, int phase, const float4* __restrict__ tgt32,
@@ -347,7 +375,7 @@ static void free_ctx(bem_ctx* c)
                     c->near_flag, c->part, c->field, c->neut, c->pts_stage, c->V, c->wvec,
                     c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
                     c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df, c->d_region,
-                    c->d_electrode};
+                    c->d_electrode, c->qnode, c->chunk_sph};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hcol_host) cudaFreeHost(c->hcol_host);
@@ -408,6 +436,7 @@ extern "C" int bem_reset_counters(bem_ctx* c)
     if (!c) return BEM_ERR_ARG;
     timing_drain(c);
     c->cnt = bem_counters{};
+    c->cnt.far32_variant = c->far32_tp;
     BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 2 * sizeof(unsigned long long), c->stream));
     BEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return BEM_OK;
@@ -464,6 +493,54 @@ extern "C" int bem_destroy(bem_ctx* ctx)
     return BEM_OK;
 }
 
+// The FP32 kernel variant (scalar, 2 or 4 packed target pairs per thread):
+// fixed by params.far32_variant, or picked by timing each candidate on two
+// matvecs of this mesh (CUDA events on the context's stream).  The work counters
+// are cleared afterwards.
+static int tune_far32(bem_ctx* c)
+{
+    if (c->prm.far32_variant != 0) {
+        c->far32_tp = c->prm.far32_variant;
+    } else if (c->np >= 4096) {
+        cudaStream_t s = c->stream;
+        cudaEvent_t e0, e1;
+        BEM_CUDA_TRY(c, cudaEventCreate(&e0));
+        BEM_CUDA_TRY(c, cudaEventCreate(&e1));
+        std::vector<double> ones(c->nunk, 1.0);
+        BEM_CUDA_TRY(c, cudaMemcpyAsync(c->zvec, ones.data(), c->nunk * sizeof(double), cudaMemcpyHostToDevice, s));
+        float best = 3e38f;
+        int best_tp = 2;
+        for (int tp : {1, 2, 4}) {
+            c->far32_tp = tp;
+            int rc = matvec_impl(c, BEM_MIXED, 1, c->zvec, c->wvec);  // warm-up
+            if (!rc) {
+                cudaEventRecord(e0, s);
+                rc = matvec_impl(c, BEM_MIXED, 1, c->zvec, c->wvec);
+                cudaEventRecord(e1, s);
+            }
+            float ms = 3e38f;
+            if (!rc && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            if (rc) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return rc;
+            }
+            if (ms < best) { best = ms; best_tp = tp; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->far32_tp = best_tp;
+    } else {
+        c->far32_tp = 2;
+    }
+    timing_drain(c);
+    c->cnt = bem_counters{};
+    c->cnt.far32_variant = c->far32_tp;
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 2 * sizeof(unsigned long long), c->stream));
+    BEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return BEM_OK;
+}
+
 static int create_impl(bem_ctx* c, const bem_mesh* mesh)
 {
     const int64_t np = c->np, nv = c->nv;
@@ -487,7 +564,8 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         (rc = dalloc(c, &c->hdr64, np)) || (rc = dalloc(c, &c->node32, Q * np)) ||
         (rc = dalloc(c, &c->node64, Q * np)) || (rc = dalloc(c, &c->tgt32, np)) ||
         (rc = dalloc(c, &c->tgt64, np)) || (rc = dalloc(c, &c->d_status, 1)) ||
-        (rc = dalloc(c, &c->node_lo32, Q * np)) || (rc = dalloc(c, &c->tgt_lo32, np)))
+        (rc = dalloc(c, &c->node_lo32, Q * np)) || (rc = dalloc(c, &c->tgt_lo32, np)) ||
+        (rc = dalloc(c, &c->qnode, Q * np)) || (rc = dalloc(c, &c->chunk_sph, (np + 31) / 32)))
         return rc;
     BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->X, mesh->X, 3 * nv * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -496,6 +574,8 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
                                                           c->hdr32, c->hdr64, c->node32, c->node64,
                                                           c->tgt32, c->tgt64, c->node_lo32,
                                                           c->tgt_lo32, c->d_status);
+    BEM_LAUNCH_CHECK(c);
+    k_chunk_spheres<<<(unsigned)(((np + 31) / 32 + 127) / 128), 128, 0, s>>>(np, c->geo, c->chunk_sph);
     BEM_LAUNCH_CHECK(c);
     int st = 0;
     BEM_CUDA_TRY(c, cudaMemcpyAsync(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
@@ -624,12 +704,17 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     // workspace: far partials for the largest launch
     const int64_t Mmax = std::max<int64_t>(np, c->prm.max_points);
     size_t need = 0;
-    for (int prec = 0; prec < 2; ++prec) {
-        for (int64_t M : {np, (int64_t)c->prm.max_points}) {
-            const size_t n = (size_t)far_splits(c, prec, M) * (size_t)M * 4 * kMaxRhs;
-            need = std::max(need, n);
+    const int tp_default = c->far32_tp;
+    for (int tp : {1, 2, 4}) {  // every FP32 kernel variant the tuner may pick
+        c->far32_tp = tp;
+        for (int prec = 0; prec < 3; ++prec) {
+            for (int64_t M : {np, (int64_t)c->prm.max_points}) {
+                const size_t n = (size_t)far_splits(c, prec, M) * (size_t)M * 4 * kMaxRhs;
+                need = std::max(need, n);
+            }
         }
     }
+    c->far32_tp = tp_default;
     (void)Mmax;
     c->part_cap = need;
     c->m = c->prm.gmres_restart;
@@ -648,6 +733,7 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         return set_err(c, BEM_ERR_NOMEM, "cudaMallocHost failed");
     }
     BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    if ((rc = tune_far32(c))) return rc;
     return BEM_OK;
 }
 
@@ -668,7 +754,9 @@ extern "C" int bem_create(bem_ctx** out, const bem_mesh* mesh, const bem_params*
     if (!(prm.eta >= 1.0) || prm.far_order < 1 || prm.far_order > kMaxOrder ||
         prm.gmres_restart < 1 || prm.gmres_restart > 1000 || prm.max_iters < 1 ||
         prm.max_refine < 1 || prm.max_points < 1 ||
-        (prm.residual != BEM_RESIDUAL_DF && prm.residual != BEM_RESIDUAL_FP64))
+        (prm.residual != BEM_RESIDUAL_DF && prm.residual != BEM_RESIDUAL_FP64) ||
+        (prm.far32_variant != 0 && prm.far32_variant != 1 && prm.far32_variant != 2 &&
+         prm.far32_variant != 4))
         return set_err(nullptr, BEM_ERR_ARG, "bad parameters (need eta >= 1, 1 <= far_order <= %d)",
                        kMaxOrder);
     for (int64_t i = 0; i < 3 * mesh->np; ++i)
