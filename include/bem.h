@@ -270,6 +270,39 @@ int bem_trace_lines(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_
                     int32_t* status_dev, int32_t* nsteps_dev, double* xend_dev);
 
 /*
+ * y = A^T x, the transpose of bem_matvec's operator (the adjoint solve needs it):
+ * column j of A integrates over triangle j the potential of point charges (rows of
+ * conductors and floating bodies) and dipoles along n_i (dielectric rows, and the
+ * neutrality rows' weights) placed at the centroids.  x_dev, y_dev: device double
+ * [N+F].  precision: BEM_FP64 or BEM_MIXED.  The first call builds a column-ordered
+ * copy of the near pairs (allocates device memory once).  far_order 2..4.
+ */
+int bem_matvec_transpose(bem_ctx* ctx, int32_t precision, const double* x_dev, double* y_dev);
+
+/*
+ * Gradient of J = sum_l w_l K_l (K_l = bem_trace_lines' breakdown integral of line
+ * l, w_l = dL_dK_dev[l]) with respect to the vertex coordinates, the conductor
+ * potentials and the permittivities, through the collocation system: for a design
+ * objective built on Eq. Breakdowncrit (the paper's outlook names optimisation;
+ * the adjoint itself is not in the paper).  u_dev must solve the system for the
+ * mesh's V0 (bem_solve, same precision).  The discrete adjoint of what bem_solve
+ * and bem_trace_lines compute: the trace is re-run with a tape, reversed step by
+ * step (located crossings enter through the implicit function theorem), A^T mu =
+ * dJ/du is solved by GMRES, and -mu^T (dA/dtheta) u + mu^T db/dtheta is summed
+ * pair by pair; regular pairs are differentiated on their quadrature nodes, near
+ * pairs through the closed form with dual numbers.
+ * Outputs (device, any may be NULL): K_dev double [L]; gX_dev double [nv][3];
+ * gV0_dev double [nregions] (dJ/dV0 of every conductor region, 0 elsewhere);
+ * geps_dev double [nregions][2] (dJ/d eps_plus, dJ/d eps_minus; eps_plus of a
+ * floating region enters its neutrality row).  Allocates temporary device memory
+ * (the tape: ~88 bytes per step and line) and synchronises.  BEM_ERR_ARG if a line
+ * ends on another electrode or in a singular field (status 2 or -1).  far_order 2..4.
+ */
+int bem_adjoint(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t L,
+                const double* seeds_dev, const bem_trace_params* tp, const double* dL_dK_dev,
+                double* K_dev, double* gX_dev, double* gV0_dev, double* geps_dev);
+
+/*
  * Field on the + side of the surface at every centroid ("E surface" of Sec. 5):
  *   E+(c_i) = E_PV(c_i) + u_i n_i / 2   (Eq. ADL read as E+.n = sigma/2 + K' sigma).
  * E_dev: device double [N][3].

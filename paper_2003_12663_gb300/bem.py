@@ -94,6 +94,9 @@ _SIGS = {
     "bem_eval_field_static": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp]),
     "bem_surface_field": (_i32, [_vp, _i32, _vp, _vp]),
     "bem_default_trace_params": (None, [ctypes.POINTER(bem_trace_params)]),
+    "bem_matvec_transpose": (_i32, [_vp, _i32, _vp, _vp]),
+    "bem_adjoint": (_i32, [_vp, _i32, _vp, _i64, _vp, ctypes.POINTER(bem_trace_params), _vp, _vp,
+                           _vp, _vp, _vp]),
     "bem_trace_lines": (_i32, [_vp, _i32, _vp, _i64, _vp, ctypes.POINTER(bem_trace_params), _vp,
                                _vp, _vp, _vp]),
 }
@@ -275,6 +278,39 @@ class Context:
         _check(lib().bem_trace_lines(self.h, precision, _ptr(u), L, _ptr(seeds), ctypes.byref(p),
                                      _ptr(K), _ptr(st), _ptr(ns), _ptr(xe)), self.h)
         return K, st, ns, xe
+
+    def _trace_params(self, tp):
+        p = bem_trace_params()
+        lib().bem_default_trace_params(ctypes.byref(p))
+        for k, v in tp.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        return p
+
+    def matvec_transpose(self, x, precision=FP64):
+        t = self._torch
+        x = self._dev(x)
+        y = t.empty_like(x)
+        _check(lib().bem_matvec_transpose(self.h, precision, _ptr(x), _ptr(y)), self.h)
+        return y
+
+    def adjoint(self, u, seeds, dL_dK, precision=FP64, **tp):
+        """bem_adjoint: (K, dJ/dX [nv,3], dJ/dV0 [nregions], dJ/deps [nregions,2])
+        for J = sum_l dL_dK[l] K_l."""
+        t = self._torch
+        p = self._trace_params(tp)
+        u = self._dev(u)
+        seeds = self._dev(seeds)
+        w = self._dev(dL_dK)
+        L = seeds.shape[0]
+        K = t.empty(L, dtype=t.float64, device="cuda")
+        gX = t.empty((len(self.X), 3), dtype=t.float64, device="cuda")
+        gV0 = t.empty(self.nregions, dtype=t.float64, device="cuda")
+        geps = t.empty((self.nregions, 2), dtype=t.float64, device="cuda")
+        _check(lib().bem_adjoint(self.h, precision, _ptr(u), L, _ptr(seeds), ctypes.byref(p), _ptr(w),
+                                 _ptr(K), _ptr(gX), _ptr(gV0), _ptr(geps)), self.h)
+        return K, gX, gV0, geps
 
     def surface_field(self, u, precision=FP64):
         t = self._torch

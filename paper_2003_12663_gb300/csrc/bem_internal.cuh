@@ -75,6 +75,11 @@ struct bem_ctx {
     int32_t* near_col = nullptr;   // [nnz]
     double4* near_val = nullptr;   // [nnz] exact (S, G) of the pair, G's normal part PV for i==j
     double4* near_val_df = nullptr;  // [nnz] what the double-FP32 pass adds (see k_near_values)
+    int64_t* csc_ptr = nullptr;    // near pairs by column (built on the first transposed product)
+    int32_t* csc_row = nullptr;
+    int64_t* csc_ent = nullptr;    // index of the pair in the row-ordered arrays
+    double4* tsrc64 = nullptr;     // [np] sources of the transposed product
+    float4* tsrc32 = nullptr;
     uint8_t* near_flag = nullptr;  // [nnz] bit0: near in FP32 classification, bit1: in FP64
 
     // workspace
@@ -230,6 +235,8 @@ int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u
 int launch_points_near(bem_ctx* ctx, int precision, int64_t M, const double* pts, const double* u,
                        const double* part, int splits, double* phi, double* E);
 int matvec_impl(bem_ctx* ctx, int precision, int nrhs, const double* x, double* y);
+// adjoint.cu: y = A^T v (one right-hand side)
+int matvecT_impl(bem_ctx* ctx, int precision, const double* v, double* y);
 
 // setup.cu
 void host_gauss_rule(int n, int weight_power, std::vector<double>& x, std::vector<double>& w);

@@ -375,7 +375,8 @@ static void free_ctx(bem_ctx* c)
                     c->near_flag, c->part, c->field, c->neut, c->pts_stage, c->V, c->wvec,
                     c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
                     c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df, c->d_region,
-                    c->d_electrode, c->qnode, c->chunk_sph};
+                    c->d_electrode, c->qnode, c->chunk_sph, c->csc_ptr, c->csc_row, c->csc_ent,
+                    c->tsrc64, c->tsrc32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hcol_host) cudaFreeHost(c->hcol_host);

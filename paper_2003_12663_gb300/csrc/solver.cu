@@ -103,10 +103,16 @@ int norm2(bem_ctx* c, const double* x, double* out_host)
     return BEM_OK;
 }
 
-// r = b - A x with the given precision
-int residual(bem_ctx* c, int precision, const double* b, const double* x, double* r)
+// y = A x or A^T x
+int apply(bem_ctx* c, int precision, bool transpose, const double* x, double* y)
 {
-    int rc = matvec_impl(c, precision, 1, x, r);
+    return transpose ? matvecT_impl(c, precision, x, y) : matvec_impl(c, precision, 1, x, y);
+}
+
+// r = b - A x (or b - A^T x) with the given precision
+int residual(bem_ctx* c, int precision, const double* b, const double* x, double* r, bool transpose = false)
+{
+    int rc = apply(c, precision, transpose, x, r);
     if (rc) return rc;
     k_resid<<<nb(c->nunk), 256, 0, c->stream>>>(r, b, c->nunk);
     BEM_LAUNCH_CHECK(c);
@@ -116,7 +122,7 @@ int residual(bem_ctx* c, int precision, const double* b, const double* x, double
 // GMRES(m) on A x = b, x in/out (device), stop at ||b - A x|| <= tol_abs.
 // Uses c->rvec, wvec, zvec, V.  iters is incremented per Arnoldi step.
 int gmres(bem_ctx* c, int precision, const double* b, double* x, bool x_zero, double tol_abs,
-          int max_iters, int* iters, double* res_out)
+          int max_iters, int* iters, double* res_out, bool transpose = false)
 {
     const int64_t n = c->nunk;
     const int m = c->m;
@@ -129,7 +135,7 @@ int gmres(bem_ctx* c, int precision, const double* b, double* x, bool x_zero, do
     int rc;
     if (x_zero) {
         BEM_CUDA_TRY(c, cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    } else if ((rc = residual(c, precision, b, x, r))) {
+    } else if ((rc = residual(c, precision, b, x, r, transpose))) {
         return rc;
     }
     double beta;
@@ -153,7 +159,7 @@ int gmres(bem_ctx* c, int precision, const double* b, double* x, bool x_zero, do
             double* vj = c->V + (int64_t)j * n;
             k_mul<<<nb(n), 256, 0, s>>>(z, c->jinv, vj, n);
             BEM_LAUNCH_CHECK(c);
-            if ((rc = matvec_impl(c, precision, 1, z, w))) return rc;
+            if ((rc = apply(c, precision, transpose, z, w))) return rc;
             // classical Gram-Schmidt, twice; h accumulates in hd[0..j]
             double* hsum = hd;
             double* htmp = hd + (m + 2);
@@ -201,12 +207,29 @@ int gmres(bem_ctx* c, int precision, const double* b, double* x, bool x_zero, do
         k_update<<<nb(n), 256, 0, s>>>(x, c->jinv, c->V, n, j, hd, n);
         BEM_LAUNCH_CHECK(c);
         // true residual of the restart
-        if ((rc = residual(c, precision, b, x, r))) return rc;
+        if ((rc = residual(c, precision, b, x, r, transpose))) return rc;
         if ((rc = norm2(c, r, &beta))) return rc;
     }
 }
 
 }  // namespace
+
+// A^T x = rhs by GMRES with the same right Jacobi scaling (diag(A^T) = diag(A));
+// x starts from 0.  Used by the adjoint.
+int solve_transpose(bem_ctx* c, int precision, const double* rhs, double* x, double tol, int* iters,
+                    double* relres)
+{
+    BEM_CUDA_TRY(c, cudaMemsetAsync(x, 0, c->nunk * sizeof(double), c->stream));
+    double bnorm;
+    if (int rc = norm2(c, rhs, &bnorm)) return rc;
+    *iters = 0;
+    *relres = 0.0;
+    if (bnorm == 0.0) return BEM_OK;
+    double res = 0.0;
+    const int rc = gmres(c, precision, rhs, x, true, tol * bnorm, c->prm.max_iters, iters, &res, true);
+    *relres = res / bnorm;
+    return rc;
+}
 
 extern "C" int bem_solve(bem_ctx* c, int32_t precision, int32_t nrhs, const double* V0,
                          double* u, double tol, int32_t* iters_out, double* relres)

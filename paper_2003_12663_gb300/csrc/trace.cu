@@ -1,194 +1,10 @@
 // trace.cu -- field lines and the breakdown integral K = int alpha_eff(|E|) ds
-// (Sec. 1, Eq. Breakdowncrit).
-//
-// One CTA traces one line.  Every field evaluation is a CTA-wide pass over all
-// triangles: regular pairs by the Duffy/Gauss rule (FP32 or FP64), the others by the
-// FP64 closed form, with the pair classification of the regular-pair kernels; the
-// per-thread partial sums are added by a fixed-order block reduction whose result
-// every thread receives.  The integrator (RK4 in arc length with K as extra state)
-// then runs identically in all threads on those broadcast values, so control flow
-// stays uniform and no thread ever waits on another beyond __syncthreads.
-//
-// Events (branch of alpha_eff at |E| = E0, |x| = r_max, entering another electrode)
-// are located on the re-stepped RK4 step by the Illinois variant of regula falsi
-// (at most 100 iterations); a step holds at most 4 events, the whole line at most
-// max_steps steps, so every loop is bounded.
-#include <cmath>
-
-#include "bem_internal.cuh"
+// (Sec. 1, Eq. Breakdowncrit): one CTA per line, the integrator of trace_core.cuh.
+#include "trace_core.cuh"
 
 namespace {
 
-constexpr int kT = 256;
-constexpr int kWarps = kT / 32;
-
-struct TArgs {
-    int64_t np;
-    const float4* hdr32;
-    const double4* hdr64;
-    const float4* node32;
-    const double4* node64;
-    const double* geo;
-    const double* u;
-    const int32_t* region;
-    const int32_t* electrode;
-    double h, r_max, c, E0, d, e_floor;
-    int64_t max_steps;
-};
-
-struct V4 {
-    double x, y, z, w;  // field (x,y,z) and the electrode indicator (w)
-};
-
-__device__ __forceinline__ double wsum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// sum over the CTA in a fixed order; every thread gets the same result
-__device__ V4 block_sum(V4 v, double* sh)
-{
-    v.x = wsum(v.x); v.y = wsum(v.y); v.z = wsum(v.z); v.w = wsum(v.w);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) {
-        sh[warp] = v.x; sh[kWarps + warp] = v.y; sh[2 * kWarps + warp] = v.z; sh[3 * kWarps + warp] = v.w;
-    }
-    __syncthreads();
-    V4 r = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        r.x += sh[w]; r.y += sh[kWarps + w]; r.z += sh[2 * kWarps + w]; r.w += sh[3 * kWarps + w];
-    }
-    return r;
-}
-
-// E(x) and the indicator sum_{j in other electrodes} G_j(x).n_j
-template <bool F32, int Q>
-__device__ __noinline__ V4 cta_field(const TArgs& A, const double* x, int seed_region, double* sh)
-{
-    const float xf = __double2float_rn(x[0]), yf = __double2float_rn(x[1]), zf = __double2float_rn(x[2]);
-    float fx = 0.f, fy = 0.f, fz = 0.f, fi = 0.f;      // FP32 regular pairs (times 4 pi)
-    double qx = 0.0, qy = 0.0, qz = 0.0, qi = 0.0;     // FP64 regular pairs (times 4 pi)
-    double nx_ = 0.0, ny_ = 0.0, nz_ = 0.0, ni = 0.0;  // closed-form pairs
-    for (int64_t j = threadIdx.x; j < A.np; j += kT) {
-        const int rj = A.region[j];
-        const bool mark = rj != seed_region && A.electrode[rj] != 0;
-        const double uj = A.u[j];
-        const double* gp = A.geo + GEO_STRIDE * j;
-        const bool far = F32 ? is_far32(xf, yf, zf, A.hdr32[j]) : is_far64(x[0], x[1], x[2], A.hdr64[j]);
-        if (far) {
-            if (F32) {
-                float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const float4 nd = A.node32[j * Q + k];
-                    const float dx = xf - nd.x, dy = yf - nd.y, dz = zf - nd.z;
-                    const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f))));
-                    const float t3 = nd.w * ri * ri * ri;
-                    gx = fmaf(t3, dx, gx); gy = fmaf(t3, dy, gy); gz = fmaf(t3, dz, gz);
-                }
-                const float uf = __double2float_rn(uj);
-                fx = fmaf(uf, gx, fx); fy = fmaf(uf, gy, fy); fz = fmaf(uf, gz, fz);
-                if (mark)
-                    fi += gx * (float)gp[GEO_N] + gy * (float)gp[GEO_N + 1] + gz * (float)gp[GEO_N + 2];
-            } else {
-                double gx = 0.0, gy = 0.0, gz = 0.0;
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const double4 nd = A.node64[j * Q + k];
-                    const double dx = x[0] - nd.x, dy = x[1] - nd.y, dz = x[2] - nd.z;
-                    const double ri = rsqrt(fma(dx, dx, fma(dy, dy, fma(dz, dz, 1e-200))));
-                    const double t3 = nd.w * ri * ri * ri;
-                    gx = fma(t3, dx, gx); gy = fma(t3, dy, gy); gz = fma(t3, dz, gz);
-                }
-                qx = fma(uj, gx, qx); qy = fma(uj, gy, qy); qz = fma(uj, gz, qz);
-                if (mark) qi += gx * gp[GEO_N] + gy * gp[GEO_N + 1] + gz * gp[GEO_N + 2];
-            }
-        } else {
-            double S, Gx, Gy, Gz;
-            tri_closed_form(gp, x[0], x[1], x[2], false, S, Gx, Gy, Gz);
-            nx_ = fma(uj, Gx, nx_); ny_ = fma(uj, Gy, ny_); nz_ = fma(uj, Gz, nz_);
-            if (mark) ni += Gx * gp[GEO_N] + Gy * gp[GEO_N + 1] + Gz * gp[GEO_N + 2];
-        }
-    }
-    V4 v;
-    v.x = nx_ + kInv4Pi * (qx + (double)fx);
-    v.y = ny_ + kInv4Pi * (qy + (double)fy);
-    v.z = nz_ + kInv4Pi * (qz + (double)fz);
-    v.w = ni + kInv4Pi * (qi + (double)fi);
-    return block_sum(v, sh);
-}
-
-__device__ __forceinline__ double norm3(double a, double b, double c) { return sqrt(a * a + b * b + c * c); }
-
-__device__ __forceinline__ double alpha_eff(const TArgs& A, double Em, int side)
-{
-    return side > 0 ? A.c * (Em - A.E0) * (Em - A.E0) : -A.d;
-}
-
-// one RK4 step of length s from (x, K); E0c: field at x if known
-template <bool F32, int Q>
-__device__ void rk4(const TArgs& A, int seed_region, double s0, int side, const double* x, double K,
-                    double s, const V4* E0c, double* x1, double& K1, double* sh)
-{
-    double k[4][3], a[4], y[3] = {x[0], x[1], x[2]};
-    for (int st = 0; st < 4; ++st) {
-        const V4 E = (st == 0 && E0c) ? *E0c : cta_field<F32, Q>(A, y, seed_region, sh);
-        const double Em = norm3(E.x, E.y, E.z);
-        k[st][0] = E.x * (s0 / Em);
-        k[st][1] = E.y * (s0 / Em);
-        k[st][2] = E.z * (s0 / Em);
-        a[st] = alpha_eff(A, Em, side);
-        if (st < 3) {
-            const double f = st < 2 ? 0.5 * s : s;
-            for (int c = 0; c < 3; ++c) y[c] = x[c] + k[st][c] * f;
-        }
-    }
-    for (int c = 0; c < 3; ++c)
-        x1[c] = x[c] + ((k[0][c] + (k[1][c] + k[2][c]) * 2.0) + k[3][c]) * (s / 6.0);
-    K1 = K + s / 6.0 * (a[0] + 2.0 * (a[1] + a[2]) + a[3]);
-}
-
-enum { EV_ALPHA = 0, EV_RMAX = 1, EV_ELECTRODE = 2 };
-
-template <bool F32, int Q>
-__device__ double event_g(const TArgs& A, int seed_region, double s0, int side, const double* x,
-                          double K, const V4* E0c, double sig, int ev, double* sh)
-{
-    double x1[3], K1;
-    rk4<F32, Q>(A, seed_region, s0, side, x, K, sig, E0c, x1, K1, sh);
-    if (ev == EV_RMAX) return norm3(x1[0], x1[1], x1[2]) - A.r_max;
-    const V4 E = cta_field<F32, Q>(A, x1, seed_region, sh);
-    if (ev == EV_ALPHA) return norm3(E.x, E.y, E.z) - A.E0;
-    return E.w + 0.5;
-}
-
-template <bool F32, int Q>
-__device__ double illinois(const TArgs& A, int seed_region, double s0, int side, const double* x,
-                           double K, const V4* E0c, double b, double ga, double gb, int ev, double* sh)
-{
-    double a = 0.0, c = b;
-    int last = 0;
-    for (int it = 0; it < 100; ++it) {
-        c = (ga * b - gb * a) / (ga - gb);
-        const double gc = event_g<F32, Q>(A, seed_region, s0, side, x, K, E0c, c, ev, sh);
-        if (gc == 0.0) break;
-        if ((gc > 0.0) == (gb > 0.0)) {
-            b = c; gb = gc;
-            if (last == -1) ga *= 0.5;
-            last = -1;
-        } else {
-            a = c; ga = gc;
-            if (last == 1) gb *= 0.5;
-            last = 1;
-        }
-        if (b - a <= 1e-14 * A.h) break;
-    }
-    return c;
-}
+using namespace tcore;
 
 template <bool F32, int Q>
 __global__ void __launch_bounds__(kT)
@@ -200,96 +16,16 @@ k_trace(TArgs A, const double* __restrict__ seeds, int64_t L, double* __restrict
     __shared__ long long s_bj[kWarps];
     const int64_t line = blockIdx.x;
     if (line >= L) return;
-    double x[3] = {seeds[3 * line], seeds[3 * line + 1], seeds[3 * line + 2]};
-    double K = 0.0;
-    // electrode of the seed: the triangle with the nearest centroid (first on ties)
-    double bd = 1e300;
-    long long bj = 0;
-    for (int64_t j = threadIdx.x; j < A.np; j += kT) {
-        const double* c = A.geo + GEO_STRIDE * j + GEO_CTR;
-        const double dd = (x[0] - c[0]) * (x[0] - c[0]) + (x[1] - c[1]) * (x[1] - c[1]) + (x[2] - c[2]) * (x[2] - c[2]);
-        if (dd < bd) { bd = dd; bj = j; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
-        const long long oj = __shfl_xor_sync(0xffffffffu, bj, o);
-        if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
-    }
-    if ((threadIdx.x & 31) == 0) { s_bd[threadIdx.x >> 5] = bd; s_bj[threadIdx.x >> 5] = bj; }
-    __syncthreads();
-    bd = s_bd[0]; bj = s_bj[0];
-    for (int w = 1; w < kWarps; ++w)
-        if (s_bd[w] < bd || (s_bd[w] == bd && s_bj[w] < bj)) { bd = s_bd[w]; bj = s_bj[w]; }
-    const int seed_region = A.region[bj];
-    const double* nb = A.geo + GEO_STRIDE * bj + GEO_N;
-    V4 E = cta_field<F32, Q>(A, x, -2, sh);
-    const double s0 = (E.x * nb[0] + E.y * nb[1] + E.z * nb[2]) >= 0.0 ? 1.0 : -1.0;
-    int side = norm3(E.x, E.y, E.z) > A.E0 ? 1 : -1;
-    int st = 3;
-    int64_t step = 0;
-    bool have = false;  // E holds the field at x (with the seed's indicator)
-    for (; step < A.max_steps; ++step) {
-        if (!have) E = cta_field<F32, Q>(A, x, seed_region, sh);
-        have = false;
-        const double Em = norm3(E.x, E.y, E.z);
-        if (!isfinite(Em)) { st = -1; break; }
-        if (Em < A.e_floor) { st = 4; break; }
-        double rem = A.h;
-        bool done = false, first = true;
-        for (int nev = 0; rem > 0.0 && nev < 4; ++nev) {
-            const V4* Ec = first ? &E : nullptr;
-            double x1[3], K1;
-            rk4<F32, Q>(A, seed_region, s0, side, x, K, rem, Ec, x1, K1, sh);
-            const V4 E1 = cta_field<F32, Q>(A, x1, seed_region, sh);
-            const double E1m = norm3(E1.x, E1.y, E1.z);
-            double best = 2.0 * rem;
-            int which = -1;
-            if ((E1m > A.E0) != (side > 0)) {
-                const double ga = event_g<F32, Q>(A, seed_region, s0, side, x, K, Ec, 0.0, EV_ALPHA, sh);
-                const double sg = illinois<F32, Q>(A, seed_region, s0, side, x, K, Ec, rem, ga, E1m - A.E0, EV_ALPHA, sh);
-                if (sg < best) { best = sg; which = EV_ALPHA; }
-            }
-            const double r1 = norm3(x1[0], x1[1], x1[2]);
-            if (r1 >= A.r_max) {
-                const double sg = illinois<F32, Q>(A, seed_region, s0, side, x, K, Ec, rem,
-                                                   norm3(x[0], x[1], x[2]) - A.r_max, r1 - A.r_max, EV_RMAX, sh);
-                if (sg < best) { best = sg; which = EV_RMAX; }
-            }
-            if (E1.w < -0.5) {
-                const double ga = event_g<F32, Q>(A, seed_region, s0, side, x, K, Ec, 0.0, EV_ELECTRODE, sh);
-                const double sg = illinois<F32, Q>(A, seed_region, s0, side, x, K, Ec, rem, ga, E1.w + 0.5, EV_ELECTRODE, sh);
-                if (sg < best) { best = sg; which = EV_ELECTRODE; }
-            }
-            if (which < 0) {
-                x[0] = x1[0]; x[1] = x1[1]; x[2] = x1[2];
-                K = K1;
-                E = E1;
-                have = true;
-                rem = 0.0;
-                break;
-            }
-            double xn[3], Kn;
-            rk4<F32, Q>(A, seed_region, s0, side, x, K, best, Ec, xn, Kn, sh);
-            x[0] = xn[0]; x[1] = xn[1]; x[2] = xn[2];
-            K = Kn;
-            first = false;
-            if (which == EV_ALPHA) {
-                side = -side;
-                rem -= best;
-                continue;
-            }
-            st = which == EV_RMAX ? 1 : 2;
-            done = true;
-            break;
-        }
-        if (done) break;
-    }
+    NoRec rec;
+    double K, xe[3];
+    int st;
+    int64_t ns;
+    trace_line<F32, Q>(A, seeds + 3 * line, rec, K, st, ns, xe, sh, s_bd, s_bj);
     if (threadIdx.x == 0) {
         if (K_out) K_out[line] = K;
         if (st_out) st_out[line] = st;
-        if (ns_out) ns_out[line] = (int32_t)step;
-        if (xe_out) { xe_out[3 * line] = x[0]; xe_out[3 * line + 1] = x[1]; xe_out[3 * line + 2] = x[2]; }
+        if (ns_out) ns_out[line] = (int32_t)ns;
+        if (xe_out) { xe_out[3 * line] = xe[0]; xe_out[3 * line + 1] = xe[1]; xe_out[3 * line + 2] = xe[2]; }
     }
 }
 
@@ -323,6 +59,20 @@ extern "C" void bem_default_trace_params(bem_trace_params* tp)
     tp->max_steps = 200000;
 }
 
+int trace_args(bem_ctx* c, const bem_trace_params* tp, const double* u, tcore::TArgs* out)
+{
+    bem_trace_params p;
+    if (tp)
+        p = *tp;
+    else
+        bem_default_trace_params(&p);
+    if (!(p.h > 0.0) || !(p.r_max > 0.0) || p.max_steps < 0 || !(p.e_floor >= 0.0))
+        return set_err(c, BEM_ERR_ARG, "trace parameters: need h > 0, r_max > 0, max_steps >= 0");
+    *out = tcore::TArgs{c->np, c->hdr32, c->hdr64, c->node32, c->node64, c->geo, u, c->d_region,
+                        c->d_electrode, p.h, p.r_max, p.c, p.E0, p.d, p.e_floor, p.max_steps};
+    return BEM_OK;
+}
+
 extern "C" int bem_trace_lines(bem_ctx* c, int32_t precision, const double* u, int64_t L,
                                const double* seeds, const bem_trace_params* tp, double* K,
                                int32_t* status, int32_t* nsteps, double* xend)
@@ -332,16 +82,9 @@ extern "C" int bem_trace_lines(bem_ctx* c, int32_t precision, const double* u, i
         return set_err(c, BEM_ERR_ARG, "precision must be BEM_FP64 or BEM_MIXED");
     if (L < 0 || L > 0x7fffffff || (L > 0 && (!u || !seeds)))
         return set_err(c, BEM_ERR_ARG, "bem_trace_lines: bad L or NULL pointer");
-    bem_trace_params p;
-    if (tp)
-        p = *tp;
-    else
-        bem_default_trace_params(&p);
-    if (!(p.h > 0.0) || !(p.r_max > 0.0) || p.max_steps < 0 || !(p.e_floor >= 0.0))
-        return set_err(c, BEM_ERR_ARG, "bem_trace_lines: need h > 0, r_max > 0, max_steps >= 0");
+    TArgs A;
+    if (int rc = trace_args(c, tp, u, &A)) return rc;
     if (L == 0) return BEM_OK;
-    TArgs A{c->np, c->hdr32, c->hdr64, c->node32, c->node64, c->geo, u, c->d_region, c->d_electrode,
-            p.h, p.r_max, p.c, p.E0, p.d, p.e_floor, p.max_steps};
     return precision == BEM_MIXED ? launch<true>(c, A, L, seeds, K, status, nsteps, xend)
                                   : launch<false>(c, A, L, seeds, K, status, nsteps, xend);
 }
