@@ -52,8 +52,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--far32-variant", type=int, default=0, choices=[0, 1, 2, 4],
                     help="FP32 regular-pair kernel variant (0: tuned at context creation)")
-    ap.add_argument("--mode", default="step", choices=["step", "matvec"],
-                    help="matvec: only W+K mixed matvecs of the workload (a small case for ncu)")
+    ap.add_argument("--mode", default="step", choices=["step", "matvec", "batch"],
+                    help="matvec: only W+K mixed matvecs of the workload (a small case for ncu); "
+                         "batch: the uneven device family solved and traced by the batched calls")
+    ap.add_argument("--instances", type=int, default=64, help="batch mode: meshes in the family")
+    ap.add_argument("--nrhs", type=int, default=4, help="batch mode: right-hand sides per mesh")
+    ap.add_argument("--seeds", type=int, default=8, help="batch mode: field lines traced per mesh")
+    ap.add_argument("--n-min", type=int, default=2000)
+    ap.add_argument("--n-max", type=int, default=30000)
     return ap.parse_args()
 
 
@@ -394,6 +400,125 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched family
+def run_batch(args):
+    """The uneven device family (seeded: triangle counts uniform in [n_min, n_max],
+    2% vertex jitter) with nrhs Dirichlet right-hand sides each (V0 in 1, 0.5, -1, 2):
+    the batched solve (persistent regular-pair launch in a graph-replayed Arnoldi
+    iteration, FP64-accurate refinement to 1e-8) and the batched tracer on a sample
+    of Fibonacci seeds per mesh.  One JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2003_12663_gb300 import bem
+    from paper_2003_12663_gb300 import meshgen as mg
+
+    meshes = mg.device_family(args.instances, n_min=args.n_min, n_max=args.n_max, seed=7)
+    ctxs = [bem.Context(m) for m in meshes]
+    nr = args.nrhs
+    vals = [1.0, 0.5, -1.0, 2.0][:nr]
+    V0 = []
+    for m in meshes:
+        V = np.zeros((nr, len(m.regions)))
+        for r, v in enumerate(vals):
+            V[r, 0] = v                     # region 0: the conductor sphere
+        V0.append(torch.tensor(V, device="cuda"))
+    B = bem.Batch(ctxs, nrhs=nr, timing=True)
+    Q = ctxs[0].params.far_order ** 2
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(3)
+    xs = [torch.tensor(rng.standard_normal((nr, c.nunk)), device=dev) for c in ctxs]
+
+    # the persistent regular-pair kernel alone (event-timed inside the library)
+    for _ in range(2):
+        B.matvec(xs)
+    B.reset_counters()
+    n_mv = 5
+    for _ in range(n_mv):
+        flush.add_(1.0)
+        B.matvec(xs)
+    cm = B.counters()
+    near = sum(c.near_pairs for c in ctxs)
+    far_pairs = cm["pairs"] / max(cm["far_launches"], 1) - near
+    flops = far_pairs * (FLOPS_PER_PAIR_OP * Q + 8 * nr)
+    far_ms = cm["far_ms"] / max(cm["far_timed"], 1)
+    props = torch.cuda.get_device_properties(dev)
+    peak, mhz = fp32_peak_tflops(props.multi_processor_count)
+    achieved = flops / (far_ms * 1e-3) / 1e12
+
+    def solve():
+        return B.solve(V0, tol=TOL, check=False)
+
+    for _ in range(args.warmup):
+        solve()
+    for c in ctxs:
+        c.reset_counters()
+    B.reset_counters()
+    clocks = ClockSampler(0)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        us, iters, rel = solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    cb = B.counters()
+    resid_pairs = sum(sum(c.counters()["pairs"]) for c in ctxs)
+    ms = float(np.mean(times))
+    value = (cb["rhs_pairs"] + resid_pairs) / args.steps / (ms * 1e-3) / 1e9
+
+    # field lines: seeds on a sphere of radius 1.05 around the conductor, mixed form
+    L = args.seeds
+    seeds = [mg.fibonacci_seeds(L, radius=1.05) for _ in ctxs]
+    u1 = [u[0] for u in us]
+    B.trace(u1, seeds, bem.MIXED)            # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    K, st, ns = B.trace(u1, seeds, bem.MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tms = e0.elapsed_time(e1)
+    steps_total = int(sum(n.sum().item() for n in ns))
+    st_all = torch.cat(st).cpu().numpy()
+    tri = [c.np for c in ctxs]
+    out = {"mode": "batch", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "dtype": "f32 regular pairs + f64",
+           "data": "synthetic (seeded meshes)",
+           "config": {"workload": f"device family: {args.instances} meshes, {min(tri)}-{max(tri)} triangles "
+                                  f"(sum {sum(tri)}), {nr} Dirichlet right-hand sides each, tol {TOL}",
+                      "instances": args.instances, "nrhs": nr, "triangles_total": sum(tri),
+                      "sum_N_squared": int(sum(t * t for t in tri)), "l2": "flushed (256 MB write) between steps"},
+           "solve": {"ms": ms, "arnoldi_steps_per_step": cb["arnoldi_steps"] / args.steps,
+                     "graph_launches_per_step": cb["graph_launches"] / args.steps,
+                     "kernel_launches_per_step": cb["kernel_launches"] / args.steps,
+                     "batched_rhs_pairs_per_step": cb["rhs_pairs"] / args.steps,
+                     "residual_pairs_per_step": resid_pairs / args.steps,
+                     "relres_max": float(rel.max()), "iters_max": int(iters.max())},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": f"k_bfar<{Q},{nr}>: persistent batched FP32 regular pairs, phi+E, {nr} rhs",
+                        "flops_per_launch": flops, "avg_launch_ms": far_ms,
+                        "flops_basis": f"far pairs x ({FLOPS_PER_PAIR_OP} x {Q} nodes + 8 x {nr} rhs)"},
+           "trace": {"lines": int(L * len(ctxs)), "ms": tms, "lines_per_s": L * len(ctxs) / (tms * 1e-3),
+                     "rk4_steps": steps_total,
+                     "status_counts": {int(k): int(v) for k, v in zip(*np.unique(st_all, return_counts=True))},
+                     "sample": f"{L} Fibonacci seeds per mesh (radius 1.05), h=1e-3, r_max=10"}}
+    if clk:
+        out["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    B.close()
+    for c in ctxs:
+        c.close()
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     world, rank, local = dist_setup(args)
@@ -443,5 +568,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.mode == "matvec":
         run_matvec(a)
+    elif a.mode == "batch":
+        run_batch(a)
     else:
         run_ours(a)

@@ -309,6 +309,88 @@ int bem_adjoint(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t L,
  */
 int bem_surface_field(bem_ctx* ctx, int32_t precision, const double* u_dev, double* E_dev);
 
+/* ------------------------------------------------------------------ batches
+ * Many meshes (instances) of uneven size with up to four right-hand sides each,
+ * served together: the operators are those of bem_matvec / bem_solve /
+ * bem_trace_lines, only scheduled for a family of devices at once.
+ *   - Regular pairs of all instances and right-hand sides run in ONE persistent
+ *     launch whose CTAs take (instance, target tile, triangle slice) work items
+ *     from an atomic counter; one pass over a pair's quadrature nodes serves all
+ *     right-hand sides of its instance.
+ *   - bem_batch_solve runs restarted GMRES(m) with right Jacobi scaling on all
+ *     systems in lock step; one Arnoldi iteration of all systems is captured once as
+ *     a CUDA graph and replayed (Hessenberg columns, rotations and stop tests on
+ *     the device).
+ *   - bem_batch_trace traces the lines of all instances in one persistent launch.
+ * The batch owns its workspace (Krylov bases: (m+1) x (N_i+F_i) doubles per system)
+ * and a private stream; every call orders itself after the work already queued on
+ * the contexts' stream and makes that stream wait for its own work, so the calls
+ * behave as if issued on the contexts' stream.  The contexts must stay alive and
+ * unused by other calls while a batch call runs.
+ */
+typedef struct bem_batch bem_batch;
+
+typedef struct {
+    int64_t n_instances, nrhs;
+    int64_t far_launches;     /* batched regular-pair launches (graph replays included) */
+    int64_t pairs;            /* (target, triangle) pairs those launches covered */
+    int64_t rhs_pairs;        /* pairs x right-hand sides */
+    int64_t graph_launches;   /* replays of the Arnoldi-iteration graph */
+    int64_t kernel_launches;  /* kernels launched by the batch, graph nodes included */
+    int64_t arnoldi_steps;    /* Arnoldi iterations summed over the systems */
+    int64_t lines;            /* field lines traced */
+    int64_t far_timed;        /* regular-pair launches timed (flags bit 0, bem_batch_matvec) */
+    double far_ms;            /* their total time in milliseconds */
+} bem_batch_counters;
+
+/*
+ * ctxs: host array of n >= 1 contexts on one device, created on one stream, with
+ * the same far_order (2..4) and gmres_restart; nrhs: right-hand sides per instance,
+ * 1..4 (system s = instance * nrhs + rhs).  flags bit 0: time the regular-pair
+ * launch of bem_batch_matvec with CUDA events (synchronises).  GMRES limits
+ * (max_iters, max_refine) and the residual form are those of ctxs[0].
+ * BEM_ERR_ARG for mismatched contexts, BEM_ERR_NOMEM if the workspace does not fit.
+ */
+int bem_batch_create(bem_batch** out, bem_ctx* const* ctxs, int32_t n, int32_t nrhs, int32_t flags);
+int bem_batch_destroy(bem_batch* b);
+const char* bem_batch_last_error(const bem_batch* b);
+int bem_batch_get_counters(bem_batch* b, bem_batch_counters* out);
+int bem_batch_reset_counters(bem_batch* b);
+
+/*
+ * y_i = A_i x_i for every instance and right-hand side, with the mixed form's
+ * products (FP32 regular pairs with compensated sums, FP64 near pairs; Eqs.
+ * Final1-Final4).  x, y: host arrays of n device pointers, each to double
+ * [nrhs][N_i+F_i].
+ */
+int bem_batch_matvec(bem_batch* b, const double* const* x, double* const* y);
+
+/*
+ * Solve A_i u_i = b_i(V0_i) for every instance and right-hand side (as bem_solve
+ * with BEM_MIXED: GMRES on the FP32-regular-pair products inside an iterative
+ * refinement whose residual uses the FP64-accurate operator) to |b - A u| <= tol |b|.
+ * precision: BEM_MIXED only.  V0: host array of n device pointers to double
+ * [nrhs][nregions_i] (conductor potentials per right-hand side), or NULL (the
+ * regions' V0, nrhs = 1).  u: host array of n device pointers to double
+ * [nrhs][N_i+F_i] (written).  iters, relres: host [n*nrhs] or NULL: Arnoldi
+ * iterations and final relative residual per system.  Synchronises.
+ * BEM_ERR_NOT_CONVERGED if a system missed tol (u holds the best iterate).
+ */
+int bem_batch_solve(bem_batch* b, int32_t precision, const double* const* V0, double* const* u,
+                    double tol, int32_t* iters, double* relres);
+
+/*
+ * Field lines of every instance (as bem_trace_lines, without the end points).
+ * u: host array of n device pointers to double [>= N_i]; L: host int64 [n] lines per
+ * instance (0 allowed); seeds: host array of n device pointers to double [L_i][3];
+ * K, status, nsteps: host arrays of n device pointers (each may be NULL, or the
+ * array itself NULL).  One persistent launch; a CTA traces one line at a time.
+ * precision BEM_FP64 or BEM_MIXED.  Synchronises.
+ */
+int bem_batch_trace(bem_batch* b, int32_t precision, const double* const* u, const int64_t* L,
+                    const double* const* seeds, const bem_trace_params* tp, double* const* K,
+                    int32_t* const* status, int32_t* const* nsteps);
+
 #ifdef __cplusplus
 }
 #endif

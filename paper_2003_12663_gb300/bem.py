@@ -74,8 +74,20 @@ class bem_counters(ctypes.Structure):
         return out
 
 
+class bem_batch_counters(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int64), ("nrhs", ctypes.c_int64),
+                ("far_launches", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("rhs_pairs", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("arnoldi_steps", ctypes.c_int64),
+                ("lines", ctypes.c_int64), ("far_timed", ctypes.c_int64), ("far_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _vp = ctypes.c_void_p
 _i32, _i64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_pvp = ctypes.POINTER(_vp)
 _SIGS = {
     "bem_default_params": (None, [ctypes.POINTER(bem_params)]),
     "bem_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(bem_mesh), ctypes.POINTER(bem_params), _vp]),
@@ -99,6 +111,16 @@ _SIGS = {
                            _vp, _vp, _vp]),
     "bem_trace_lines": (_i32, [_vp, _i32, _vp, _i64, _vp, ctypes.POINTER(bem_trace_params), _vp,
                                _vp, _vp, _vp]),
+    "bem_batch_create": (_i32, [_pvp, _pvp, _i32, _i32, _i32]),
+    "bem_batch_destroy": (_i32, [_vp]),
+    "bem_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "bem_batch_get_counters": (_i32, [_vp, ctypes.POINTER(bem_batch_counters)]),
+    "bem_batch_reset_counters": (_i32, [_vp]),
+    "bem_batch_matvec": (_i32, [_vp, _pvp, _pvp]),
+    "bem_batch_solve": (_i32, [_vp, _i32, _pvp, _pvp, _dbl, ctypes.POINTER(_i32),
+                               ctypes.POINTER(_dbl)]),
+    "bem_batch_trace": (_i32, [_vp, _i32, _pvp, ctypes.POINTER(_i64), _pvp,
+                               ctypes.POINTER(bem_trace_params), _pvp, _pvp, _pvp]),
 }
 _lib = None
 
@@ -325,3 +347,109 @@ class Context:
         A = t.empty((row1 - row0, self.nunk), dtype=t.float64, device="cuda")
         _check(lib().bem_assemble_rows(self.h, row0, row1, precision, _ptr(A), self.nunk), self.h)
         return A
+
+
+def _ptr_array(tensors):
+    """Host array of device pointers (None -> NULL entries)."""
+    return (_vp * len(tensors))(*[None if t is None else t.data_ptr() for t in tensors])
+
+
+class Batch:
+    """bem_batch: several Contexts (one device, one stream, one far_order in 2..4,
+    one gmres_restart) with nrhs right-hand sides each, served by one persistent
+    regular-pair launch, a CUDA-graph Arnoldi iteration and one persistent tracer
+    launch.  The contexts are kept alive by this object."""
+
+    def __init__(self, contexts, nrhs=1, timing=False):
+        import torch
+        self._torch = torch
+        self.contexts = list(contexts)
+        self.nrhs = int(nrhs)
+        arr = (_vp * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = _vp()
+        rc = lib().bem_batch_create(ctypes.byref(h), arr, len(self.contexts), self.nrhs,
+                                    1 if timing else 0)
+        if rc != 0:
+            raise BemError(rc, "bem_batch_create: contexts must share device, stream, far_order "
+                               "(2..4) and gmres_restart; 1 <= nrhs <= 4")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = lib().bem_batch_last_error(self.h)
+            raise BemError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bem_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def counters(self) -> dict:
+        c = bem_batch_counters()
+        self._check(lib().bem_batch_get_counters(self.h, ctypes.byref(c)))
+        return c.as_dict()
+
+    def reset_counters(self):
+        self._check(lib().bem_batch_reset_counters(self.h))
+
+    def _vecs(self, xs):
+        t = self._torch
+        out = []
+        for c, x in zip(self.contexts, xs):
+            x = x if isinstance(x, t.Tensor) else t.as_tensor(np.asarray(x))
+            out.append(x.to(device="cuda", dtype=t.float64).reshape(self.nrhs, c.nunk).contiguous())
+        return out
+
+    def matvec(self, xs):
+        """y_i = A_i x_i (mixed form) for every instance; xs: per instance [nrhs][nunk_i]."""
+        t = self._torch
+        xs = self._vecs(xs)
+        ys = [t.empty_like(x) for x in xs]
+        self._check(lib().bem_batch_matvec(self.h, _ptr_array(xs), _ptr_array(ys)))
+        return ys
+
+    def solve(self, V0=None, tol=1e-8, precision=MIXED, check=True):
+        """u_i [nrhs][nunk_i] per instance, Arnoldi iterations and relative residuals
+        [n][nrhs].  V0: per instance [nrhs][nregions_i] conductor potentials, or None."""
+        t = self._torch
+        n, nr = len(self.contexts), self.nrhs
+        v = None
+        if V0 is not None:
+            v = [(x if isinstance(x, t.Tensor) else t.as_tensor(np.asarray(x))).to(
+                device="cuda", dtype=t.float64).reshape(nr, c.nregions).contiguous()
+                 for c, x in zip(self.contexts, V0)]
+        us = [t.empty((nr, c.nunk), dtype=t.float64, device="cuda") for c in self.contexts]
+        it = (_i32 * (n * nr))()
+        rel = (_dbl * (n * nr))()
+        rc = lib().bem_batch_solve(self.h, precision, None if v is None else _ptr_array(v),
+                                   _ptr_array(us), tol, it, rel)
+        if check or rc not in (0, -4):
+            self._check(rc)
+        return us, np.array(it[:]).reshape(n, nr), np.array(rel[:]).reshape(n, nr)
+
+    def trace(self, us, seeds, precision=MIXED, **tp):
+        """Lines of every instance in one launch: lists of K, status, nsteps (device)."""
+        t = self._torch
+        p = bem_trace_params()
+        lib().bem_default_trace_params(ctypes.byref(p))
+        for k, val in tp.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, val)
+        us = [u.to(device="cuda", dtype=t.float64).reshape(-1).contiguous() for u in us]
+        sd = [(s if isinstance(s, t.Tensor) else t.as_tensor(np.asarray(s))).to(
+            device="cuda", dtype=t.float64).reshape(-1, 3).contiguous() for s in seeds]
+        L = (_i64 * len(sd))(*[len(s) for s in sd])
+        K = [t.empty(len(s), dtype=t.float64, device="cuda") for s in sd]
+        st = [t.empty(len(s), dtype=t.int32, device="cuda") for s in sd]
+        ns = [t.empty(len(s), dtype=t.int32, device="cuda") for s in sd]
+        self._check(lib().bem_batch_trace(self.h, precision, _ptr_array(us), L, _ptr_array(sd),
+                                          ctypes.byref(p), _ptr_array(K), _ptr_array(st),
+                                          _ptr_array(ns)))
+        return K, st, ns

@@ -963,8 +963,10 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     if (off.alloc(L) || cap.alloc(L) || nrec.alloc(L) || s0s.alloc(L) || Kf.alloc(L) || sr.alloc(L) ||
         stt.alloc(L))
         return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
-    k_adj_forward<F32, Q><<<(unsigned)L, kT, 0, s>>>(A, seeds, L, nullptr, off.p, cap.p, nrec.p, s0s.p,
-                                                     sr.p, Kf.p, stt.p);
+    constexpr size_t fsm = field_smem<F32, Q>();
+    BEM_CUDA_TRY(c, allow_smem(k_adj_forward<F32, Q>, fsm));
+    k_adj_forward<F32, Q><<<(unsigned)L, kT, fsm, s>>>(A, seeds, L, nullptr, off.p, cap.p, nrec.p, s0s.p,
+                                                       sr.p, Kf.p, stt.p);
     BEM_LAUNCH_CHECK(c);
     std::vector<int64_t> h_n(L), h_off(L);
     std::vector<int32_t> h_st(L);
@@ -983,8 +985,8 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     if (tape.alloc(tot)) return set_err(c, BEM_ERR_NOMEM, "adjoint: tape of %lld steps", (long long)tot);
     BEM_CUDA_TRY(c, cudaMemcpyAsync(off.p, h_off.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(cap.p, h_n.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    k_adj_forward<F32, Q><<<(unsigned)L, kT, 0, s>>>(A, seeds, L, tape.p, off.p, cap.p, nrec.p, s0s.p,
-                                                     sr.p, Kf.p, stt.p);
+    k_adj_forward<F32, Q><<<(unsigned)L, kT, fsm, s>>>(A, seeds, L, tape.p, off.p, cap.p, nrec.p, s0s.p,
+                                                       sr.p, Kf.p, stt.p);
     BEM_LAUNCH_CHECK(c);
     if (K_out) BEM_CUDA_TRY(c, cudaMemcpyAsync(K_out, Kf.p, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
 

@@ -52,6 +52,7 @@ struct bem_ctx {
     float4* qnode = nullptr;      // [np][Q] FP32 nodes with sigma folded into w (per call)
     float4* chunk_sph = nullptr;  // [np/32 rounded up] bounding sphere of 32 triangles' near zones
     int far32_tp = 2;             // FP32 kernel variant: 1 scalar, 2 or 4 packed target pairs
+    float4* nrm32 = nullptr;      // [np] (unit normal in FP32, region index as int bits): field lines
     float4* tgt_lo32 = nullptr;   // [np] centroid - tgt32
     float4* tgt32 = nullptr;    // [np] centroids          FP32
     double4* tgt64 = nullptr;   // [np] centroids          FP64

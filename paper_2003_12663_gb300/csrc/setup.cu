@@ -228,6 +228,19 @@ __global__ void k_panels(int64_t np, int g, double eta, const double* __restrict
     }
 }
 
+// Per triangle for the field-line integrator: the unit normal rounded to FP32 and
+// the region index (as the bits of w), so that one 16-byte record carries what the
+// electrode indicator needs.
+__global__ void k_nrm32(int64_t np, const double* __restrict__ geo, const int32_t* __restrict__ region,
+                        float4* __restrict__ out)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const double* g = geo + GEO_STRIDE * j;
+    out[j] = make_float4(__double2float_rn(g[GEO_N]), __double2float_rn(g[GEO_N + 1]),
+                         __double2float_rn(g[GEO_N + 2]), __int_as_float(region[j]));
+}
+
 // Bounding sphere of the near zones |x - cc_j| <= eta R_j of 32 consecutive
 // triangles, enlarged by a margin that covers the FP32 rounding of the
 // classification: a target farther than the radius from the centre is regular
@@ -376,7 +389,7 @@ static void free_ctx(bem_ctx* c)
                     c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
                     c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df, c->d_region,
                     c->d_electrode, c->qnode, c->chunk_sph, c->csc_ptr, c->csc_row, c->csc_ent,
-                    c->tsrc64, c->tsrc32};
+                    c->tsrc64, c->tsrc32, c->nrm32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hcol_host) cudaFreeHost(c->hcol_host);
@@ -689,9 +702,13 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         std::vector<int32_t> elec(nreg);
         for (int r = 0; r < nreg; ++r)
             elec[r] = (c->regions[r].kind == BEM_CONDUCTOR || c->regions[r].kind == BEM_FLOATING) ? 1 : 0;
-        if ((rc = dalloc(c, &c->d_region, np)) || (rc = dalloc(c, &c->d_electrode, nreg))) return rc;
+        if ((rc = dalloc(c, &c->d_region, np)) || (rc = dalloc(c, &c->d_electrode, nreg)) ||
+            (rc = dalloc(c, &c->nrm32, np)))
+            return rc;
         BEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_region, c->h_region.data(), np * 4, cudaMemcpyHostToDevice, s));
         BEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_electrode, elec.data(), nreg * 4, cudaMemcpyHostToDevice, s));
+        k_nrm32<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(np, c->geo, c->d_region, c->nrm32);
+        BEM_LAUNCH_CHECK(c);
         BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
     }
     if (!fr.empty())

@@ -35,8 +35,11 @@ int launch(bem_ctx* c, const TArgs& A, int64_t L, const double* seeds, double* K
 {
     const unsigned grid = (unsigned)L;
     switch (c->g) {
-#define TR_CASE(G, QQ) \
-    case G: k_trace<F32, QQ><<<grid, kT, 0, c->stream>>>(A, seeds, L, K, st, ns, xe); break;
+#define TR_CASE(G, QQ)                                                                             \
+    case G:                                                                                        \
+        BEM_CUDA_TRY(c, allow_smem(k_trace<F32, QQ>, field_smem<F32, QQ>()));                      \
+        k_trace<F32, QQ><<<grid, kT, field_smem<F32, QQ>(), c->stream>>>(A, seeds, L, K, st, ns, xe); \
+        break;
         TR_CASE(1, 1) TR_CASE(2, 4) TR_CASE(3, 9) TR_CASE(4, 16) TR_CASE(5, 25) TR_CASE(6, 36)
 #undef TR_CASE
         default: return set_err(c, BEM_ERR_ARG, "far_order %d not compiled", c->g);
@@ -69,7 +72,7 @@ int trace_args(bem_ctx* c, const bem_trace_params* tp, const double* u, tcore::T
     if (!(p.h > 0.0) || !(p.r_max > 0.0) || p.max_steps < 0 || !(p.e_floor >= 0.0))
         return set_err(c, BEM_ERR_ARG, "trace parameters: need h > 0, r_max > 0, max_steps >= 0");
     *out = tcore::TArgs{c->np, c->hdr32, c->hdr64, c->node32, c->node64, c->geo, u, c->d_region,
-                        c->d_electrode, p.h, p.r_max, p.c, p.E0, p.d, p.e_floor, p.max_steps};
+                        c->d_electrode, p.h, p.r_max, p.c, p.E0, p.d, p.e_floor, p.max_steps, c->nrm32};
     return BEM_OK;
 }
 

@@ -37,7 +37,70 @@ struct TArgs {
     const int32_t* electrode;
     double h, r_max, c, E0, d, e_floor;
     int64_t max_steps;
+    const float4* nrm32;  // [np] FP32 normal, region index in the bits of w
 };
+
+// The FP32 field evaluation streams the triangles through shared memory in chunks
+// of TC (nodes, classification header, normal + region, density), double-buffered
+// with asynchronous copies so the loads of chunk c+1 overlap the work on chunk c.
+// Thread t takes triangle c*TC + t of every chunk: with TC = kT that is the
+// triangle sequence t, t + kT, t + 2 kT, ... of a plain strided loop.
+template <int Q>
+struct Stage32 {
+    static constexpr int TC = Q <= 16 ? kT : kT / 2;  // larger rules: half chunks fit the 227 KB
+    float4 node[2][TC * Q];
+    float4 hdr[2][TC];
+    float4 nrm[2][TC];
+    double u[2][TC];
+};
+
+// dynamic shared memory a kernel running trace_line<F32, Q> must be launched with
+template <bool F32, int Q>
+constexpr size_t field_smem()
+{
+    return F32 ? sizeof(Stage32<Q>) : 0;
+}
+
+// allow a kernel more than the default 48 KB of dynamic shared memory
+template <class Kernel>
+inline cudaError_t allow_smem(Kernel k, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+__device__ __forceinline__ void cp_async16(void* s, const void* g)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void* s, const void* g)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// issue the copies of triangles [c0, c0 + n) into buffer b
+template <int Q>
+__device__ __forceinline__ void stage_chunk(const TArgs& A, Stage32<Q>& S, int b, int64_t c0, int n)
+{
+    const float4* gn = A.node32 + c0 * Q;
+    for (int k = threadIdx.x; k < n * Q; k += kT) cp_async16(&S.node[b][k], gn + k);
+    for (int k = threadIdx.x; k < n; k += kT) {
+        cp_async16(&S.hdr[b][k], A.hdr32 + c0 + k);
+        cp_async16(&S.nrm[b][k], A.nrm32 + c0 + k);
+        cp_async8(&S.u[b][k], A.u + c0 + k);
+    }
+}
 
 struct V4 {
     double x, y, z, w;  // field (x,y,z) and the electrode indicator (w)
@@ -76,28 +139,65 @@ __device__ __noinline__ V4 cta_field(const TArgs& A, const double* x, int seed_r
     float fx = 0.f, fy = 0.f, fz = 0.f, fi = 0.f;      // FP32 regular pairs (times 4 pi)
     double qx = 0.0, qy = 0.0, qz = 0.0, qi = 0.0;     // FP64 regular pairs (times 4 pi)
     double nx_ = 0.0, ny_ = 0.0, nz_ = 0.0, ni = 0.0;  // closed-form pairs
-    for (int64_t j = threadIdx.x; j < A.np; j += kT) {
-        const int rj = A.region[j];
-        const bool mark = rj != seed_region && A.electrode[rj] != 0;
-        const double uj = A.u[j];
+    // a near pair: the closed form in FP64
+    auto near_pair = [&](int64_t j, double uj, bool mark) {
         const double* gp = A.geo + GEO_STRIDE * j;
-        const bool far = F32 ? is_far32(xf, yf, zf, A.hdr32[j]) : is_far64(x[0], x[1], x[2], A.hdr64[j]);
-        if (far) {
-            if (F32) {
-                float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const float4 nd = A.node32[j * Q + k];
-                    const float dx = xf - nd.x, dy = yf - nd.y, dz = zf - nd.z;
-                    const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f))));
-                    const float t3 = nd.w * ri * ri * ri;
-                    gx = fmaf(t3, dx, gx); gy = fmaf(t3, dy, gy); gz = fmaf(t3, dz, gz);
-                }
-                const float uf = __double2float_rn(uj);
-                fx = fmaf(uf, gx, fx); fy = fmaf(uf, gy, fy); fz = fmaf(uf, gz, fz);
-                if (mark)
-                    fi += gx * (float)gp[GEO_N] + gy * (float)gp[GEO_N + 1] + gz * (float)gp[GEO_N + 2];
+        double S, Gx, Gy, Gz;
+        tri_closed_form(gp, x[0], x[1], x[2], false, S, Gx, Gy, Gz);
+        nx_ = fma(uj, Gx, nx_); ny_ = fma(uj, Gy, ny_); nz_ = fma(uj, Gz, nz_);
+        if (mark) ni += Gx * gp[GEO_N] + Gy * gp[GEO_N + 1] + Gz * gp[GEO_N + 2];
+    };
+    if constexpr (F32) {
+        extern __shared__ __align__(16) unsigned char tcore_dyn[];
+        Stage32<Q>& S = *reinterpret_cast<Stage32<Q>*>(tcore_dyn);
+        constexpr int TC = Stage32<Q>::TC;
+        const int64_t nch = (A.np + TC - 1) / TC;
+        const int t = threadIdx.x;
+        stage_chunk<Q>(A, S, 0, 0, (int)min((int64_t)TC, A.np));
+        cp_async_commit();
+        for (int64_t c = 0; c < nch; ++c) {
+            const int b = (int)(c & 1);
+            if (c + 1 < nch) {
+                const int64_t c1 = (c + 1) * TC;
+                stage_chunk<Q>(A, S, b ^ 1, c1, (int)min((int64_t)TC, A.np - c1));
+                cp_async_commit();
+                cp_async_wait<1>();
             } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const int64_t j = c * TC + t;
+            if (t < TC && j < A.np) {
+                const float4 nv = S.nrm[b][t];
+                const int rj = __float_as_int(nv.w);
+                const bool mark = rj != seed_region && A.electrode[rj] != 0;
+                const double uj = S.u[b][t];
+                if (is_far32(xf, yf, zf, S.hdr[b][t])) {
+                    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) {
+                        const float4 nd = S.node[b][t * Q + k];
+                        const float dx = xf - nd.x, dy = yf - nd.y, dz = zf - nd.z;
+                        const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f))));
+                        const float t3 = nd.w * ri * ri * ri;
+                        gx = fmaf(t3, dx, gx); gy = fmaf(t3, dy, gy); gz = fmaf(t3, dz, gz);
+                    }
+                    const float uf = __double2float_rn(uj);
+                    fx = fmaf(uf, gx, fx); fy = fmaf(uf, gy, fy); fz = fmaf(uf, gz, fz);
+                    if (mark) fi += gx * nv.x + gy * nv.y + gz * nv.z;
+                } else {
+                    near_pair(j, uj, mark);
+                }
+            }
+            __syncthreads();  // buffer b is refilled in the next iteration
+        }
+    } else {
+        for (int64_t j = threadIdx.x; j < A.np; j += kT) {
+            const int rj = A.region[j];
+            const bool mark = rj != seed_region && A.electrode[rj] != 0;
+            const double uj = A.u[j];
+            if (is_far64(x[0], x[1], x[2], A.hdr64[j])) {
+                const double* gp = A.geo + GEO_STRIDE * j;
                 double gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
@@ -109,12 +209,9 @@ __device__ __noinline__ V4 cta_field(const TArgs& A, const double* x, int seed_r
                 }
                 qx = fma(uj, gx, qx); qy = fma(uj, gy, qy); qz = fma(uj, gz, qz);
                 if (mark) qi += gx * gp[GEO_N] + gy * gp[GEO_N + 1] + gz * gp[GEO_N + 2];
+            } else {
+                near_pair(j, uj, mark);
             }
-        } else {
-            double S, Gx, Gy, Gz;
-            tri_closed_form(gp, x[0], x[1], x[2], false, S, Gx, Gy, Gz);
-            nx_ = fma(uj, Gx, nx_); ny_ = fma(uj, Gy, ny_); nz_ = fma(uj, Gz, nz_);
-            if (mark) ni += Gx * gp[GEO_N] + Gy * gp[GEO_N + 1] + Gz * gp[GEO_N + 2];
         }
     }
     V4 v;

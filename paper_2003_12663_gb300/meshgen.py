@@ -331,6 +331,18 @@ def device_mesh(scale: float = 1.0, seed: int = 2, jitter_frac: float = 0.005,
     return Mesh(X, tri, region, regions, info)
 
 
+def device_family(n: int = 64, n_min: int = 2000, n_max: int = 30000, seed: int = 7,
+                  jitter_frac: float = 0.02) -> list:
+    """n seeded perturbations of device_mesh for batched runs: triangle counts drawn
+    uniformly in [n_min, n_max] (through the scale; counts grow like scale**2 from
+    about 20k at scale 1) and every vertex jittered by up to jitter_frac of its mean
+    edge length per coordinate."""
+    rng = np.random.default_rng(seed)
+    target = rng.uniform(n_min, n_max, size=n)
+    return [device_mesh(scale=math.sqrt(t / 20068.0), seed=seed * 1000 + 3 * k, jitter_frac=jitter_frac)
+            for k, t in enumerate(target)]
+
+
 # --------------------------------------------------------------------------- points
 def ball_points(M: int, rmax: float, rng) -> np.ndarray:
     """M points uniform in the ball |x| < rmax (rejection sampling from the cube)."""
