@@ -52,9 +52,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--far32-variant", type=int, default=0, choices=[0, 1, 2, 4],
                     help="FP32 regular-pair kernel variant (0: tuned at context creation)")
-    ap.add_argument("--mode", default="step", choices=["step", "matvec", "batch"],
+    ap.add_argument("--mode", default="step", choices=["step", "matvec", "batch", "report", "trace"],
                     help="matvec: only W+K mixed matvecs of the workload (a small case for ncu); "
-                         "batch: the uneven device family solved and traced by the batched calls")
+                         "batch: the uneven device family solved and traced by the batched calls; "
+                         "report: per-configuration times and errors of both GPU forms and the oracle")
+    ap.add_argument("--report-configs", default="c1,c2,c3,c5", help="report mode: configurations")
+    ap.add_argument("--c5-lines", type=int, default=64, help="report mode: field lines traced on c5")
+    ap.add_argument("--lines", type=int, default=512, help="trace mode: field lines")
+    ap.add_argument("--max-steps", type=int, default=200000, help="trace mode: RK4 step limit per line")
     ap.add_argument("--instances", type=int, default=64, help="batch mode: meshes in the family")
     ap.add_argument("--nrhs", type=int, default=4, help="batch mode: right-hand sides per mesh")
     ap.add_argument("--seeds", type=int, default=8, help="batch mode: field lines traced per mesh")
@@ -519,6 +524,187 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ field lines alone
+def run_trace(args):
+    """bem_trace_lines on the device workload (mixed form): --lines Fibonacci seeds on
+    |x| = 1.05 around the conductor sphere, h = 1e-3, r_max = 10; one warm-up call on
+    8 lines, then the timed call.  Reports lines/s and field-evaluation pair-ops/s."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2003_12663_gb300 import bem
+    from paper_2003_12663_gb300 import meshgen as mg
+    mesh = mg.device_mesh(args.scale, seed=2)
+    ctx = bem.Context(mesh)
+    u, _, _ = ctx.solve(bem.MIXED, tol=TOL)
+    seeds = torch.tensor(mg.fibonacci_seeds(args.lines, radius=1.05))
+    ctx.trace_lines(u[0], seeds[:8], bem.MIXED, max_steps=args.max_steps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    K, st, ns, xe = ctx.trace_lines(u[0], seeds, bem.MIXED, max_steps=args.max_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    steps = int(ns.sum().item())
+    Q = ctx.params.far_order ** 2
+    print(json.dumps({"mode": "trace", "triangles": ctx.np, "lines": args.lines, "ms": ms,
+                      "lines_per_s": args.lines / (ms * 1e-3), "rk4_steps": steps,
+                      "field_pair_ops_per_s": steps * 4 * ctx.np * Q / (ms * 1e-3),
+                      "status_counts": {int(k): int(v) for k, v in
+                                        zip(*np.unique(st.cpu().numpy(), return_counts=True))}}), flush=True)
+    ctx.close()
+
+
+# ------------------------------------------------------------------ per-configuration report
+def K_sphere_closed(V0=1.0, c=1e-2, E0=0.5, d=0.1, rmax=10.0):
+    """K along a radial line from the unit sphere at V0 (continuum field V0 x / |x|^3):
+    int_1^rs c (V0/r^2 - E0)^2 dr - d (rmax - rs), rs = sqrt(V0/E0)."""
+    rs = (V0 / E0) ** 0.5
+    F = lambda r: c * (-V0 * V0 / (3 * r ** 3) + 2 * V0 * E0 / r + E0 * E0 * r)
+    return F(rs) - F(1.0) - d * (rmax - rs)
+
+
+def run_report(args):
+    """One JSON line per configuration: set-up / solve / field / trace / adjoint times
+    of the FP64 and mixed GPU forms (CUDA events), the oracle's time on a stated
+    sample (host cores), and the errors against closed forms and the oracle."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2003_12663_gb300 import bem
+    from paper_2003_12663_gb300 import meshgen as mg
+    from oracle import oracle as O
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) * 1e3
+
+    def emit(d):
+        d["cores"] = os.cpu_count()
+        print(json.dumps(d), flush=True)
+
+    want = set(args.report_configs.split(","))
+    if "c1" in want:
+        mesh = mg.sphere_mesh(3)
+        pts = mg.sphere_eval_points(1, 1000, 1000)
+        pts_d = torch.tensor(pts, device="cuda")
+        P = O.Problem(mesh, eta=4.0, g=3)
+        A_o, t_asm = wall(lambda: P.assemble())
+        u_o, t_lu = wall(lambda: np.linalg.solve(A_o, P.rhs()))
+        (phi_o, E_o), t_fo = wall(lambda: P.field(u_o, pts))
+        out = {"config": "c1 sphere, 1,280 triangles, V0=1, tol 1e-10, 2,000 points",
+               "oracle_ms": {"assemble": t_asm, "lu_solve": t_lu, "field": t_fo}}
+        for name, prec in (("fp64", bem.FP64), ("mixed", bem.MIXED)):
+            ctx, t_set = wall(lambda: bem.Context(mesh))
+            _, t_rows = timed(lambda: ctx.assemble_rows(precision=prec))
+            (u, it, rel), t_sol = timed(lambda: ctx.solve(prec, tol=1e-10))
+            (phi, E), t_ev = timed(lambda: ctx.eval_field(u[0], pts_d, prec))
+            ug, phig, Eg = u[0].cpu().numpy(), phi.cpu().numpy(), E.cpu().numpy()
+            inside = np.linalg.norm(pts, axis=1) < 1.0
+            out[name] = {"setup_ms": t_set, "assemble_rows_ms": t_rows, "solve_ms": t_sol, "iters": it,
+                         "eval_ms": t_ev, "relres": rel[0],
+                         "sigma_rel_l2_vs_oracle": float(np.linalg.norm(ug - u_o) / np.linalg.norm(u_o)),
+                         "sigma_rms_vs_exact_1": float(np.sqrt(np.mean((ug - 1.0) ** 2))),
+                         "phi_inside_max_dev_from_1": float(np.abs(phig[inside] - 1.0).max()),
+                         "E_inside_max": float(np.linalg.norm(Eg[inside], axis=1).max()),
+                         "E_rel_vs_oracle": float(np.abs(Eg - E_o).max() / np.abs(E_o).max())}
+            ctx.close()
+        emit(out)
+    if "c2" in want:
+        mesh = mg.device_mesh(1.0, seed=2)
+        pts = mg.device_box_points(100000, seed=5)
+        pts_d = torch.tensor(pts, device="cuda")
+        out = {"config": f"c2 device, {mesh.np_} triangles, tol 1e-8, 1e5 points"}
+        res = {}
+        for name, prec in (("fp64", bem.FP64), ("mixed", bem.MIXED)):
+            ctx, t_set = wall(lambda: bem.Context(mesh))
+            (u, it, rel), t_sol = timed(lambda: ctx.solve(prec, tol=TOL))
+            Es, t_sf = timed(lambda: ctx.surface_field(u[0], prec))
+            (phi, E), t_ev = timed(lambda: ctx.eval_field(u[0], pts_d, prec))
+            res[name] = (u[0], E)
+            out[name] = {"setup_ms": t_set, "solve_ms": t_sol, "iters": it, "relres": rel[0],
+                         "surface_field_ms": t_sf, "eval_ms": t_ev}
+            ctx.close()
+        u64, E64 = res["fp64"]
+        um, Em = res["mixed"]
+        out["mixed"]["sigma_rel_l2_vs_fp64"] = (torch.linalg.norm(um - u64) / torch.linalg.norm(u64)).item()
+        out["mixed"]["E_rel_vs_fp64"] = ((Em - E64).abs().max() / E64.abs().max()).item()
+        # oracle: pair integrals of a seeded sample of rows, extrapolated to the N^2 pairs
+        rate, rows, secs = cpu_oracle_rate(mesh, 8.0)
+        out["oracle"] = {"pairs_per_s": rate, "sample": f"{rows} rows x {mesh.np_} triangles, {secs:.1f} s",
+                         "one_product_s_extrapolated": mesh.np_ ** 2 / rate}
+        sel = np.random.default_rng(9).choice(len(pts), 500, replace=False)
+        P = O.Problem(mesh, eta=4.0, g=3)
+        _, E_o = P.field(u64.cpu().numpy(), pts[sel])
+        out["fp64"]["E_rel_vs_oracle_500pts"] = float(np.abs(E64.cpu().numpy()[sel] - E_o).max() / np.abs(E_o).max())
+        out["mixed"]["E_rel_vs_oracle_500pts"] = float(np.abs(Em.cpu().numpy()[sel] - E_o).max() / np.abs(E_o).max())
+        emit(out)
+    if "c3" in want:
+        mesh = mg.sphere_mesh(3)
+        seeds = torch.tensor(mg.fibonacci_seeds(256))
+        Kc = K_sphere_closed()
+        dKc = (K_sphere_closed(1.0 + 1e-6) - K_sphere_closed(1.0 - 1e-6)) / 2e-6
+        out = {"config": "c3 sphere 1,280 triangles, 256 Fibonacci lines, h=1e-3, r_max=10",
+               "K_closed_per_line": Kc, "dK_dV0_closed_per_line": dKc}
+        ctx = bem.Context(mesh)
+        for name, prec in (("fp64", bem.FP64), ("mixed", bem.MIXED)):
+            (u, it, rel), t_sol = timed(lambda: ctx.solve(prec, tol=1e-12 if prec == bem.FP64 else 1e-10))
+            (K, st, ns, xe), t_tr = timed(lambda: ctx.trace_lines(u[0], seeds, prec))
+            w = torch.ones(256, dtype=torch.float64, device="cuda")
+            (Ka, gX, gV0, geps), t_adj = timed(lambda: ctx.adjoint(u[0], seeds, w, prec))
+            Kn = K.cpu().numpy()
+            out[name] = {"solve_ms": t_sol, "trace_ms": t_tr, "adjoint_ms": t_adj,
+                         "rk4_steps": int(ns.sum().item()), "status_1": int((st == 1).sum().item()),
+                         "K_sum": float(Kn.sum()), "K_mean_abs_err_vs_closed": float(np.abs(Kn - Kc).mean()),
+                         "dK_dV0_per_line": gV0[0].item() / 256}
+        # oracle tracer on 4 of the lines (FP64 field of the method), extrapolated to 256
+        P = O.Problem(mesh, eta=4.0, g=3)
+        u64, _, _ = ctx.solve(bem.FP64, tol=1e-12)
+        (Ko, so, no, xo), t_o = wall(lambda: P.trace(u64[0].cpu().numpy(), mg.fibonacci_seeds(256)[:4]))
+        out["oracle"] = {"trace_4_lines_ms": t_o, "trace_256_lines_s_extrapolated": t_o * 64 / 1e3}
+        ctx.close()
+        emit(out)
+    if "c5" in want:
+        scale = (200000 / 20068.0) ** 0.5
+        mesh = mg.device_mesh(scale, seed=2)
+        pts = mg.device_box_points(1000000, seed=5)
+        pts_d = torch.tensor(pts, device="cuda")
+        ctx, t_set = wall(lambda: bem.Context(mesh))
+        (u, it, rel), t_sol = timed(lambda: ctx.solve(bem.MIXED, tol=TOL))
+        (phi, E), t_ev = timed(lambda: ctx.eval_field(u[0], pts_d, bem.MIXED))
+        x = u[0]
+        _, t_mv32 = timed(lambda: ctx.matvec(x, bem.MIXED))
+        _, t_mv64 = timed(lambda: ctx.matvec(x, bem.FP64))
+        L = args.c5_lines
+        seeds = torch.tensor(mg.fibonacci_seeds(L, radius=1.05))
+        (K, st, ns, xe), t_tr = timed(lambda: ctx.trace_lines(u[0], seeds, bem.MIXED))
+        sel = np.random.default_rng(5).choice(len(pts), 1000, replace=False)
+        P = O.Problem(mesh, eta=4.0, g=3)
+        (_, E_o), t_o = wall(lambda: P.field(u[0].cpu().numpy(), pts[sel]))
+        emit({"config": f"c5 device at {mesh.np_} triangles, mixed to {TOL}, 1e6 box points, {L} lines (sample)",
+              "mixed": {"setup_ms": t_set, "solve_ms": t_sol, "iters": it, "relres": rel[0], "eval_ms": t_ev,
+                        "trace_ms": t_tr, "rk4_steps": int(ns.sum().item()),
+                        "E_rel_vs_oracle_1000pts": float(np.abs(E.cpu().numpy()[sel] - E_o).max() / np.abs(E_o).max())},
+              "matvec_ms": {"mixed": t_mv32, "fp64": t_mv64},
+              "fp64_solve_s_extrapolated": it * t_mv64 / 1e3,
+              "oracle": {"field_1000pts_ms": t_o, "field_1e6pts_s_extrapolated": t_o / 1e3 * 1000}})
+        ctx.close()
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     world, rank, local = dist_setup(args)
@@ -570,5 +756,9 @@ if __name__ == "__main__":
         run_matvec(a)
     elif a.mode == "batch":
         run_batch(a)
+    elif a.mode == "report":
+        run_report(a)
+    elif a.mode == "trace":
+        run_trace(a)
     else:
         run_ours(a)

@@ -55,7 +55,7 @@ struct TapeRec {
     __device__ void step(int64_t st, const double* x, double K, int side)
     {
         n = st + 1;
-        if (st < cap && threadIdx.x == 0) {
+        if (st < cap && (threadIdx.x & 31) == 0) {
             StepRec& r = tape[st];
             r.x[0] = x[0]; r.x[1] = x[1]; r.x[2] = x[2];
             r.K = K;
@@ -65,7 +65,7 @@ struct TapeRec {
     }
     __device__ void sub(int64_t st, int k, double sig, int kind)
     {
-        if (st < cap && k < 4 && threadIdx.x == 0) {
+        if (st < cap && k < 4 && (threadIdx.x & 31) == 0) {
             tape[st].sig[k] = sig;
             tape[st].kind[k] = kind;
             tape[st].nsub = k + 1;
@@ -73,31 +73,33 @@ struct TapeRec {
     }
 };
 
-// forward with a tape (cap 0: count the records only)
+// forward with a tape (cap 0: count the records only): the persistent tracer
+// launch of bem_trace_lines, with a recorder per line
 template <bool F32, int Q>
-__global__ void __launch_bounds__(kT)
-k_adj_forward(TArgs A, const double* __restrict__ seeds, int64_t L, StepRec* tape,
-              const int64_t* __restrict__ off, const int64_t* __restrict__ cap,
+__global__ void __launch_bounds__(kLT)
+k_adj_forward(TArgs A, const double* __restrict__ seeds, int64_t L, unsigned long long* __restrict__ next,
+              StepRec* tape, const int64_t* __restrict__ off, const int64_t* __restrict__ cap,
               int64_t* __restrict__ nrec, double* __restrict__ s0_out, int* __restrict__ sr_out,
               double* __restrict__ K_out, int32_t* __restrict__ st_out)
 {
-    __shared__ double sh[4 * kWarps];
-    __shared__ double s_bd[kWarps];
-    __shared__ long long s_bj[kWarps];
-    const int64_t line = blockIdx.x;
-    if (line >= L) return;
-    TapeRec rec{tape ? tape + off[line] : nullptr, tape ? cap[line] : 0, 0, 1.0, -1};
-    double K, xe[3];
-    int st;
-    int64_t ns;
-    trace_line<F32, Q>(A, seeds + 3 * line, rec, K, st, ns, xe, sh, s_bd, s_bj);
-    if (threadIdx.x == 0) {
-        nrec[line] = rec.n;
-        s0_out[line] = rec.s0;
-        sr_out[line] = rec.seed_region;
-        K_out[line] = K;
-        st_out[line] = st;
-    }
+    __shared__ Round R;
+    __shared__ TArgs sA;
+    __shared__ int s_inst;
+    run_lines<F32, Q>([&](int) { return A; }, [&](int) { return L; }, 1, next, sA, R, s_inst,
+                      [&](const TArgs& a, Round& r, int, int64_t line) {
+                          TapeRec rec{tape ? tape + off[line] : nullptr, tape ? cap[line] : 0, 0, 1.0, -1};
+                          double K, xe[3];
+                          int st;
+                          int64_t ns;
+                          trace_line<F32, Q>(a, r, seeds + 3 * line, rec, K, st, ns, xe);
+                          if ((threadIdx.x & 31) == 0) {
+                              nrec[line] = rec.n;
+                              s0_out[line] = rec.s0;
+                              sr_out[line] = rec.seed_region;
+                              K_out[line] = K;
+                              st_out[line] = st;
+                          }
+                      });
 }
 
 // ---------------------------------------------------------------- CTA passes
@@ -965,8 +967,10 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
         return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
     constexpr size_t fsm = field_smem<F32, Q>();
     BEM_CUDA_TRY(c, allow_smem(k_adj_forward<F32, Q>, fsm));
-    k_adj_forward<F32, Q><<<(unsigned)L, kT, fsm, s>>>(A, seeds, L, nullptr, off.p, cap.p, nrec.p, s0s.p,
-                                                       sr.p, Kf.p, stt.p);
+    const unsigned fgrid = lines_grid(k_adj_forward<F32, Q>, fsm, c->num_sms, L);
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), s));
+    k_adj_forward<F32, Q><<<fgrid, kLT, fsm, s>>>(A, seeds, L, c->d_line_next, nullptr, off.p, cap.p, nrec.p,
+                                                  s0s.p, sr.p, Kf.p, stt.p);
     BEM_LAUNCH_CHECK(c);
     std::vector<int64_t> h_n(L), h_off(L);
     std::vector<int32_t> h_st(L);
@@ -985,8 +989,9 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     if (tape.alloc(tot)) return set_err(c, BEM_ERR_NOMEM, "adjoint: tape of %lld steps", (long long)tot);
     BEM_CUDA_TRY(c, cudaMemcpyAsync(off.p, h_off.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(cap.p, h_n.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    k_adj_forward<F32, Q><<<(unsigned)L, kT, fsm, s>>>(A, seeds, L, tape.p, off.p, cap.p, nrec.p, s0s.p,
-                                                       sr.p, Kf.p, stt.p);
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), s));
+    k_adj_forward<F32, Q><<<fgrid, kLT, fsm, s>>>(A, seeds, L, c->d_line_next, tape.p, off.p, cap.p, nrec.p,
+                                                  s0s.p, sr.p, Kf.p, stt.p);
     BEM_LAUNCH_CHECK(c);
     if (K_out) BEM_CUDA_TRY(c, cudaMemcpyAsync(K_out, Kf.p, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
 

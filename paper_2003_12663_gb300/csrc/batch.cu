@@ -549,52 +549,32 @@ __global__ void k_bmask_jn(const SysState* st, int nsys, int* mask)
 }
 
 // ---------------------------------------------------------------- field lines
+// the persistent tracer over all meshes: a CTA traces lines of one mesh at a time
+// (per-mesh line counters in next[]), then moves to another mesh with lines left
 template <bool F32, int Q>
-__global__ void __launch_bounds__(tcore::kT)
+__global__ void __launch_bounds__(tcore::kLT)
 k_btrace(const tcore::TArgs* __restrict__ args, const int64_t* __restrict__ loff, int ninst,
-         const double* const* __restrict__ seeds, double* const* __restrict__ Kout,
-         int32_t* const* __restrict__ stout, int32_t* const* __restrict__ nsout,
-         unsigned long long* __restrict__ queue)
+         unsigned long long* __restrict__ next, const double* const* __restrict__ seeds,
+         double* const* __restrict__ Kout, int32_t* const* __restrict__ stout,
+         int32_t* const* __restrict__ nsout)
 {
-    __shared__ double sh[4 * tcore::kWarps];
-    __shared__ double s_bd[tcore::kWarps];
-    __shared__ long long s_bj[tcore::kWarps];
+    __shared__ tcore::Round R;
     __shared__ tcore::TArgs sA;
-    __shared__ long long s_line;
     __shared__ int s_inst;
-    const int64_t total = loff[ninst];
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const long long g = (long long)atomicAdd(queue, 1ull);
-            int lo = 0;
-            if (g < total) {
-                int hi = ninst - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (loff[mid] <= g) lo = mid; else hi = mid - 1;
-                }
-                sA = args[lo];
+    tcore::run_lines<F32, Q>(
+        [&](int i) { return args[i]; }, [&](int i) { return loff[i + 1] - loff[i]; }, ninst, next, sA, R, s_inst,
+        [&](const tcore::TArgs& a, tcore::Round& r, int i, int64_t l) {
+            tcore::NoRec rec;
+            double K, xe[3];
+            int st;
+            int64_t ns;
+            tcore::trace_line<F32, Q>(a, r, seeds[i] + 3 * l, rec, K, st, ns, xe);
+            if ((threadIdx.x & 31) == 0) {
+                if (Kout[i]) Kout[i][l] = K;
+                if (stout[i]) stout[i][l] = st;
+                if (nsout[i]) nsout[i][l] = (int32_t)ns;
             }
-            s_line = g;
-            s_inst = lo;
-        }
-        __syncthreads();
-        const long long g = s_line;
-        const int ii = s_inst;
-        if (g >= total) break;
-        const int64_t l = g - loff[ii];
-        tcore::NoRec rec;
-        double K, xe[3];
-        int st;
-        int64_t ns;
-        tcore::trace_line<F32, Q>(sA, seeds[ii] + 3 * l, rec, K, st, ns, xe, sh, s_bd, s_bj);
-        if (threadIdx.x == 0) {
-            if (Kout[ii]) Kout[ii][l] = K;
-            if (stout[ii]) stout[ii][l] = st;
-            if (nsout[ii]) nsout[ii][l] = (int32_t)ns;
-        }
-        __syncthreads();  // sA and s_line are rewritten by thread 0 next
-    }
+        });
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -639,7 +619,8 @@ struct bem_batch {
     Sys* d_sys = nullptr;
     SysState* d_st = nullptr;
     int64_t* d_item_off = nullptr;
-    unsigned long long* d_queue = nullptr;  // [2]: regular-pair items, field lines
+    unsigned long long* d_queue = nullptr;  // work counter of the regular-pair items
+    unsigned long long* d_lnext = nullptr;  // [n] line counters of the tracer
     unsigned long long* d_pairs = nullptr;
     int* d_j = nullptr;
     int* d_count = nullptr;
@@ -789,7 +770,7 @@ extern "C" int bem_batch_create(bem_batch** out, bem_ctx* const* ctxs, int32_t n
     b->total_items = item_off[n];
     const int ns = b->nsys;
     ok = ok && dalloc(b, &b->d_inst, n) && dalloc(b, &b->d_sys, ns) && dalloc(b, &b->d_st, ns) &&
-         dalloc(b, &b->d_item_off, n + 1) && dalloc(b, &b->d_queue, 2) && dalloc(b, &b->d_pairs, 1) &&
+         dalloc(b, &b->d_item_off, n + 1) && dalloc(b, &b->d_queue, 1) && dalloc(b, &b->d_lnext, n) && dalloc(b, &b->d_pairs, 1) &&
          dalloc(b, &b->d_j, 1) && dalloc(b, &b->d_count, 1) && dalloc(b, &b->d_alive, ns) &&
          dalloc(b, &b->d_mask, ns) && dalloc(b, &b->d_all, ns) && dalloc(b, &b->d_upd, ns) &&
          dalloc(b, &b->d_targs, n) && dalloc(b, &b->d_loff, n + 1) && dalloc(b, &b->d_tptr, 4 * (size_t)n);
@@ -1185,26 +1166,21 @@ extern "C" int bem_batch_trace(bem_batch* b, int32_t precision, const double* co
     BB_TRY(b, cudaMemcpyAsync(b->d_targs, A.data(), n * sizeof(tcore::TArgs), cudaMemcpyHostToDevice, s));
     BB_TRY(b, cudaMemcpyAsync(b->d_loff, loff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     BB_TRY(b, cudaMemcpyAsync(b->d_tptr, ptrs.data(), ptrs.size() * sizeof(void*), cudaMemcpyHostToDevice, s));
-    BB_TRY(b, cudaMemsetAsync(b->d_queue + 1, 0, sizeof(unsigned long long), s));
+    BB_TRY(b, cudaMemsetAsync(b->d_lnext, 0, n * sizeof(unsigned long long), s));
     const double* const* d_seeds = (const double* const*)b->d_tptr;
     double* const* d_K = (double* const*)(b->d_tptr + n);
     int32_t* const* d_st = (int32_t* const*)(b->d_tptr + 2 * n);
     int32_t* const* d_ns = (int32_t* const*)(b->d_tptr + 3 * n);
-    int per_sm = 1;
     int rc = BEM_OK;
     switch (b->g * 2 + (precision == BEM_MIXED ? 1 : 0)) {
-#define BT(G, QQ, F32)                                                                                   \
-    case G * 2 + F32: {                                                                                  \
-        constexpr size_t fsm = tcore::field_smem<F32, QQ>();                                             \
-        BB_TRY(b, tcore::allow_smem(k_btrace<F32, QQ>, fsm));                                            \
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_btrace<F32, QQ>, tcore::kT, fsm) != \
-            cudaSuccess)                                                                                 \
-            per_sm = 1;                                                                                  \
-        const unsigned grid =                                                                            \
-            (unsigned)std::min<int64_t>(total, (int64_t)b->num_sms * std::max(per_sm, 1));               \
-        k_btrace<F32, QQ><<<grid, tcore::kT, fsm, s>>>(b->d_targs, b->d_loff, n, d_seeds, d_K, d_st,     \
-                                                       d_ns, b->d_queue + 1);                            \
-        break;                                                                                           \
+#define BT(G, QQ, F32)                                                                                  \
+    case G * 2 + F32: {                                                                                 \
+        constexpr size_t fsm = tcore::field_smem<F32, QQ>();                                            \
+        BB_TRY(b, tcore::allow_smem(k_btrace<F32, QQ>, fsm));                                           \
+        const unsigned grid = tcore::lines_grid(k_btrace<F32, QQ>, fsm, b->num_sms, total);             \
+        k_btrace<F32, QQ><<<grid, tcore::kLT, fsm, s>>>(b->d_targs, b->d_loff, n, b->d_lnext, d_seeds,  \
+                                                        d_K, d_st, d_ns);                               \
+        break;                                                                                          \
     }
         BT(2, 4, 0) BT(2, 4, 1) BT(3, 9, 0) BT(3, 9, 1) BT(4, 16, 0) BT(4, 16, 1)
 #undef BT

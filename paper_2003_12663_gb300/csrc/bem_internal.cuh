@@ -53,6 +53,7 @@ struct bem_ctx {
     float4* chunk_sph = nullptr;  // [np/32 rounded up] bounding sphere of 32 triangles' near zones
     int far32_tp = 2;             // FP32 kernel variant: 1 scalar, 2 or 4 packed target pairs
     float4* nrm32 = nullptr;      // [np] (unit normal in FP32, region index as int bits): field lines
+    float* u32 = nullptr;         // [np] density rounded to FP32 for the field-line integrator
     float4* tgt_lo32 = nullptr;   // [np] centroid - tgt32
     float4* tgt32 = nullptr;    // [np] centroids          FP32
     double4* tgt64 = nullptr;   // [np] centroids          FP64
@@ -102,6 +103,7 @@ struct bem_ctx {
     double* hcol = nullptr;        // [2(m+2)] device Hessenberg column scratch
     double* hcol_host = nullptr;   // pinned mirror
     int* d_status = nullptr;       // device-side status word
+    unsigned long long* d_line_next = nullptr;  // line counter of the persistent tracer launches
 
     // work counters (bem_counters) and optional kernel timing
     bem_counters cnt{};

@@ -489,17 +489,19 @@ __device__ __forceinline__ df32 df_from(double v)
 // Regular pairs in double-FP32, centroid targets only (the refinement residual).
 // Near pairs are masked with the FP32 classification, exactly as in k_far32; the
 // consumer adds per near pair the value that turns the result into the FP64
-// classification's (see k_near_values).
-template <int TR, int Q>
+// classification's (see k_near_values).  NR right-hand sides (densities
+// u + r * ustride) share one pass over the nodes: the node sums of a pair do not
+// depend on the density; each right-hand side's arithmetic is that of NR = 1.
+template <int TR, int Q, int NR>
 __global__ void __launch_bounds__(kThreads)
 k_far_df(const float4* __restrict__ t32, const float4* __restrict__ t32lo, int64_t M,
          const float4* __restrict__ hdr, const float4* __restrict__ node,
-         const float4* __restrict__ node_lo, const double* __restrict__ u, int64_t np,
-         int64_t per_split, double* __restrict__ part)
+         const float4* __restrict__ node_lo, const double* __restrict__ u, int64_t ustride,
+         int64_t np, int64_t per_split, double* __restrict__ part)
 {
     constexpr int PC = 16;
     __shared__ float4 s_hdr[PC];
-    __shared__ float2 s_u[PC];
+    __shared__ float2 s_u[NR][PC];
     __shared__ float4 s_node[PC * Q];
     __shared__ float4 s_nlo[PC * Q];
     const int tid = threadIdx.x;
@@ -517,19 +519,24 @@ k_far_df(const float4* __restrict__ t32, const float4* __restrict__ t32lo, int64
         tx[r] = {h.x, l.x}; ty[r] = {h.y, l.y}; tz[r] = {h.z, l.z};
         fx[r] = h.x; fy[r] = h.y; fz[r] = h.z;
     }
-    df32 acc[TR][4];
+    df32 acc[NR][TR][4];
 #pragma unroll
-    for (int r = 0; r < TR; ++r)
+    for (int q = 0; q < NR; ++q)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = {0.f, 0.f};
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[q][r][c] = {0.f, 0.f};
 
     for (int64_t c0 = p0; c0 < p1; c0 += PC) {
         const int npc = (int)min((int64_t)PC, p1 - c0);
         __syncthreads();
         for (int k = tid; k < npc; k += kThreads) {
             s_hdr[k] = hdr[c0 + k];
-            const df32 v = df_from(u[c0 + k]);
-            s_u[k] = make_float2(v.hi, v.lo);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const df32 v = df_from(u[q * ustride + c0 + k]);
+                s_u[q][k] = make_float2(v.hi, v.lo);
+            }
         }
         for (int k = tid; k < npc * Q; k += kThreads) {
             s_node[k] = node[c0 * Q + k];
@@ -564,27 +571,32 @@ k_far_df(const float4* __restrict__ t32, const float4* __restrict__ t32lo, int64
                 }
             }
             const float4 h = s_hdr[p];
-            const float2 up = s_u[p];
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
                 const bool far = is_far32(fx[r], fy[r], fz[r], h);
-                const df32 m = far ? df32{up.x, up.y} : df32{0.f, 0.f};
-                acc[r][0] = df_add(acc[r][0], df_mul(m, ps[r]));
-                acc[r][1] = df_add(acc[r][1], df_mul(m, gx[r]));
-                acc[r][2] = df_add(acc[r][2], df_mul(m, gy[r]));
-                acc[r][3] = df_add(acc[r][3], df_mul(m, gz[r]));
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    const float2 up = s_u[q][p];
+                    const df32 m = far ? df32{up.x, up.y} : df32{0.f, 0.f};
+                    acc[q][r][0] = df_add(acc[q][r][0], df_mul(m, ps[r]));
+                    acc[q][r][1] = df_add(acc[q][r][1], df_mul(m, gx[r]));
+                    acc[q][r][2] = df_add(acc[q][r][2], df_mul(m, gy[r]));
+                    acc[q][r][3] = df_add(acc[q][r][3], df_mul(m, gz[r]));
+                }
             }
         }
     }
 #pragma unroll
-    for (int r = 0; r < TR; ++r) {
-        const int64_t t = base + r * kThreads + tid;
-        if (t < M) {
-            double* o = part + ((int64_t)split * M + t) * 4;
+    for (int q = 0; q < NR; ++q)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) o[c] = (double)acc[r][c].hi + (double)acc[r][c].lo;
+        for (int r = 0; r < TR; ++r) {
+            const int64_t t = base + r * kThreads + tid;
+            if (t < M) {
+                double* o = part + (((int64_t)q * gridDim.y + split) * M + t) * 4;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) o[c] = (double)acc[q][r][c].hi + (double)acc[q][r][c].lo;
+            }
         }
-    }
 }
 
 template <int Q>
@@ -617,8 +629,8 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
     } else if (precision == kPrecDF) {
         if (raw || !T.t32lo) return set_err(ctx, BEM_ERR_ARG, "double-FP32 pass needs centroid targets");
         dim3 grid((unsigned)((T.M + kThreads * kTRdf - 1) / (kThreads * kTRdf)), (unsigned)splits);
-        k_far_df<kTRdf, Q><<<grid, kThreads, 0, ctx->stream>>>(
-            T.t32, T.t32lo, T.M, ctx->hdr32, ctx->node32, ctx->node_lo32, u, np, per_split, part);
+        k_far_df<kTRdf, Q, 1><<<grid, kThreads, 0, ctx->stream>>>(
+            T.t32, T.t32lo, T.M, ctx->hdr32, ctx->node32, ctx->node_lo32, u, 0, np, per_split, part);
     } else if (precision == BEM_MIXED) {
         dim3 grid((unsigned)((T.M + kThreads * kTR32 - 1) / (kThreads * kTR32)), (unsigned)splits);
         if (raw)
@@ -636,6 +648,30 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
             k_far64<kTR64, Q, false><<<grid, kThreads, 0, ctx->stream>>>(
                 T.t64, nullptr, T.M, ctx->hdr64, ctx->node64, u, np, per_split, part);
     }
+    BEM_LAUNCH_CHECK(ctx);
+    return BEM_OK;
+}
+
+// double-FP32 pass of nrhs (2..4) right-hand sides in one launch (g = 2..4)
+template <int Q>
+int launch_df_multi(bem_ctx* ctx, const FarTargets& T, const double* u, int nrhs, int64_t ustride,
+                    int splits, double* part)
+{
+    if (T.tpts || !T.t32lo) return set_err(ctx, BEM_ERR_ARG, "double-FP32 pass needs centroid targets");
+    const int64_t np = ctx->np;
+    const int64_t per_split = ((np + splits - 1) / splits + kPC32 - 1) / kPC32 * kPC32;
+    dim3 grid((unsigned)((T.M + kThreads * kTRdf - 1) / (kThreads * kTRdf)), (unsigned)splits);
+#define DFM(NR)                                                                                       \
+    k_far_df<kTRdf, Q, NR><<<grid, kThreads, 0, ctx->stream>>>(T.t32, T.t32lo, T.M, ctx->hdr32,         \
+                                                               ctx->node32, ctx->node_lo32, u, ustride, \
+                                                               np, per_split, part)
+    switch (nrhs) {
+        case 2: DFM(2); break;
+        case 3: DFM(3); break;
+        case 4: DFM(4); break;
+        default: return set_err(ctx, BEM_ERR_ARG, "double-FP32 pass: nrhs %d", nrhs);
+    }
+#undef DFM
     BEM_LAUNCH_CHECK(ctx);
     return BEM_OK;
 }
@@ -662,6 +698,21 @@ int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u
 {
     if (T.M <= 0) return BEM_OK;
     const int pi = precision;  // BEM_FP64, BEM_MIXED or kPrecDF
+    if (precision == kPrecDF && nrhs > 1 && ctx->g >= 2 && ctx->g <= 4) {
+        // all right-hand sides in one pass; part holds [nrhs][splits][M][4]
+        ctx->cnt.far_launches[pi] += 1;
+        ctx->cnt.pairs[pi] += nrhs * T.M * ctx->np;
+        if (T.tpts == nullptr) ctx->cnt.near_pairs[pi] += nrhs * ctx->nnz_prec[pi];
+        timing_begin(ctx, pi);
+        int rc;
+        switch (ctx->g) {
+            case 2: rc = launch_df_multi<4>(ctx, T, u, nrhs, ustride, splits, part); break;
+            case 3: rc = launch_df_multi<9>(ctx, T, u, nrhs, ustride, splits, part); break;
+            default: rc = launch_df_multi<16>(ctx, T, u, nrhs, ustride, splits, part); break;
+        }
+        timing_end(ctx);
+        return rc;
+    }
     for (int r = 0; r < nrhs; ++r) {
         const double* ur = u + r * ustride;
         double* pr = part + (size_t)r * splits * T.M * 4;

@@ -389,7 +389,7 @@ static void free_ctx(bem_ctx* c)
                     c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
                     c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df, c->d_region,
                     c->d_electrode, c->qnode, c->chunk_sph, c->csc_ptr, c->csc_row, c->csc_ent,
-                    c->tsrc64, c->tsrc32, c->nrm32};
+                    c->tsrc64, c->tsrc32, c->nrm32, c->d_line_next, c->u32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hcol_host) cudaFreeHost(c->hcol_host);
@@ -578,6 +578,7 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         (rc = dalloc(c, &c->hdr64, np)) || (rc = dalloc(c, &c->node32, Q * np)) ||
         (rc = dalloc(c, &c->node64, Q * np)) || (rc = dalloc(c, &c->tgt32, np)) ||
         (rc = dalloc(c, &c->tgt64, np)) || (rc = dalloc(c, &c->d_status, 1)) ||
+        (rc = dalloc(c, &c->d_line_next, 1)) ||
         (rc = dalloc(c, &c->node_lo32, Q * np)) || (rc = dalloc(c, &c->tgt_lo32, np)) ||
         (rc = dalloc(c, &c->qnode, Q * np)) || (rc = dalloc(c, &c->chunk_sph, (np + 31) / 32)))
         return rc;
@@ -703,7 +704,7 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         for (int r = 0; r < nreg; ++r)
             elec[r] = (c->regions[r].kind == BEM_CONDUCTOR || c->regions[r].kind == BEM_FLOATING) ? 1 : 0;
         if ((rc = dalloc(c, &c->d_region, np)) || (rc = dalloc(c, &c->d_electrode, nreg)) ||
-            (rc = dalloc(c, &c->nrm32, np)))
+            (rc = dalloc(c, &c->nrm32, np)) || (rc = dalloc(c, &c->u32, np)))
             return rc;
         BEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_region, c->h_region.data(), np * 4, cudaMemcpyHostToDevice, s));
         BEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_electrode, elec.data(), nreg * 4, cudaMemcpyHostToDevice, s));

@@ -1,45 +1,62 @@
 // trace.cu -- field lines and the breakdown integral K = int alpha_eff(|E|) ds
-// (Sec. 1, Eq. Breakdowncrit): one CTA per line, the integrator of trace_core.cuh.
+// (Sec. 1, Eq. Breakdowncrit): a persistent launch of tracer CTAs, each tracing up
+// to kLW lines at a time with the integrator of trace_core.cuh.
 #include "trace_core.cuh"
 
 namespace {
 
 using namespace tcore;
 
-template <bool F32, int Q>
-__global__ void __launch_bounds__(kT)
-k_trace(TArgs A, const double* __restrict__ seeds, int64_t L, double* __restrict__ K_out,
-        int32_t* __restrict__ st_out, int32_t* __restrict__ ns_out, double* __restrict__ xe_out)
+// u32 = u rounded to FP32 (the density of the tracer's regular pairs)
+__global__ void k_density32(int64_t np, const double* __restrict__ u, float* __restrict__ u32)
 {
-    __shared__ double sh[4 * kWarps];
-    __shared__ double s_bd[kWarps];
-    __shared__ long long s_bj[kWarps];
-    const int64_t line = blockIdx.x;
-    if (line >= L) return;
-    NoRec rec;
-    double K, xe[3];
-    int st;
-    int64_t ns;
-    trace_line<F32, Q>(A, seeds + 3 * line, rec, K, st, ns, xe, sh, s_bd, s_bj);
-    if (threadIdx.x == 0) {
-        if (K_out) K_out[line] = K;
-        if (st_out) st_out[line] = st;
-        if (ns_out) ns_out[line] = (int32_t)ns;
-        if (xe_out) { xe_out[3 * line] = xe[0]; xe_out[3 * line + 1] = xe[1]; xe_out[3 * line + 2] = xe[2]; }
-    }
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < np) u32[i] = __double2float_rn(u[i]);
+}
+
+template <bool F32, int Q>
+__global__ void __launch_bounds__(kLT)
+k_trace(TArgs A, const double* __restrict__ seeds, int64_t L, unsigned long long* __restrict__ next,
+        double* __restrict__ K_out, int32_t* __restrict__ st_out, int32_t* __restrict__ ns_out,
+        double* __restrict__ xe_out)
+{
+    __shared__ Round R;
+    __shared__ TArgs sA;
+    __shared__ int s_inst;
+    run_lines<F32, Q>([&](int) { return A; }, [&](int) { return L; }, 1, next, sA, R, s_inst,
+                      [&](const TArgs& a, Round& r, int, int64_t line) {
+                          NoRec rec;
+                          double K, xe[3];
+                          int st;
+                          int64_t ns;
+                          trace_line<F32, Q>(a, r, seeds + 3 * line, rec, K, st, ns, xe);
+                          if ((threadIdx.x & 31) == 0) {
+                              if (K_out) K_out[line] = K;
+                              if (st_out) st_out[line] = st;
+                              if (ns_out) ns_out[line] = (int32_t)ns;
+                              if (xe_out) {
+                                  xe_out[3 * line] = xe[0];
+                                  xe_out[3 * line + 1] = xe[1];
+                                  xe_out[3 * line + 2] = xe[2];
+                              }
+                          }
+                      });
 }
 
 template <bool F32>
 int launch(bem_ctx* c, const TArgs& A, int64_t L, const double* seeds, double* K, int32_t* st,
            int32_t* ns, double* xe)
 {
-    const unsigned grid = (unsigned)L;
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), c->stream));
     switch (c->g) {
-#define TR_CASE(G, QQ)                                                                             \
-    case G:                                                                                        \
-        BEM_CUDA_TRY(c, allow_smem(k_trace<F32, QQ>, field_smem<F32, QQ>()));                      \
-        k_trace<F32, QQ><<<grid, kT, field_smem<F32, QQ>(), c->stream>>>(A, seeds, L, K, st, ns, xe); \
-        break;
+#define TR_CASE(G, QQ)                                                                           \
+    case G: {                                                                                    \
+        constexpr size_t fsm = field_smem<F32, QQ>();                                            \
+        BEM_CUDA_TRY(c, allow_smem(k_trace<F32, QQ>, fsm));                                      \
+        const unsigned grid = lines_grid(k_trace<F32, QQ>, fsm, c->num_sms, L);                  \
+        k_trace<F32, QQ><<<grid, kLT, fsm, c->stream>>>(A, seeds, L, c->d_line_next, K, st, ns, xe); \
+        break;                                                                                   \
+    }
         TR_CASE(1, 1) TR_CASE(2, 4) TR_CASE(3, 9) TR_CASE(4, 16) TR_CASE(5, 25) TR_CASE(6, 36)
 #undef TR_CASE
         default: return set_err(c, BEM_ERR_ARG, "far_order %d not compiled", c->g);
@@ -72,7 +89,12 @@ int trace_args(bem_ctx* c, const bem_trace_params* tp, const double* u, tcore::T
     if (!(p.h > 0.0) || !(p.r_max > 0.0) || p.max_steps < 0 || !(p.e_floor >= 0.0))
         return set_err(c, BEM_ERR_ARG, "trace parameters: need h > 0, r_max > 0, max_steps >= 0");
     *out = tcore::TArgs{c->np, c->hdr32, c->hdr64, c->node32, c->node64, c->geo, u, c->d_region,
-                        c->d_electrode, p.h, p.r_max, p.c, p.E0, p.d, p.e_floor, p.max_steps, c->nrm32};
+                        c->d_electrode, p.h, p.r_max, p.c, p.E0, p.d, p.e_floor, p.max_steps, c->nrm32,
+                        c->u32};
+    if (u) {  // the FP32 density of the regular pairs, on the context's stream
+        k_density32<<<(unsigned)((c->np + 255) / 256), 256, 0, c->stream>>>(c->np, u, c->u32);
+        BEM_LAUNCH_CHECK(c);
+    }
     return BEM_OK;
 }
 

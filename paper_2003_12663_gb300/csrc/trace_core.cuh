@@ -1,29 +1,38 @@
-// trace_core.cuh -- the field-line integrator shared by bem_trace_lines and the
-// adjoint's recording forward pass (Sec. 1, Eq. Breakdowncrit), so that both
-// compute the same trajectory bit for bit.
+// trace_core.cuh -- the field-line integrator shared by bem_trace_lines,
+// bem_batch_trace and the adjoint's recording forward pass (Sec. 1, Eq.
+// Breakdowncrit), so that all of them compute the same trajectory bit for bit.
 //
-// One CTA traces one line.  Every field evaluation is a CTA-wide pass over all
-// triangles: regular pairs by the Duffy/Gauss rule (FP32 or FP64), the others by the
-// FP64 closed form, with the pair classification of the regular-pair kernels; the
-// per-thread partial sums are added by a fixed-order block reduction whose result
-// every thread receives.  The integrator (RK4 in arc length with K as extra state)
-// then runs identically in all threads on those broadcast values, so control flow
-// stays uniform and no thread ever waits on another beyond __syncthreads.
+// A tracer CTA of kLW warps traces up to kLW lines at a time, one per warp.  Each
+// warp runs the integrator of its own line (RK4 in arc length with K as extra
+// state, FP64, identical in all 32 lanes so control flow is warp-uniform).  Field
+// evaluations are collective rounds: every warp posts the point it needs (or
+// nothing), then all threads evaluate the field at all posted points in one pass
+// over the triangles -- each staged quadrature node serves every posted target --
+// and each warp takes its own result.  Regular pairs by the Duffy/Gauss rule (FP32
+// or FP64), the other pairs by the FP64 closed form, with the pair classification of
+// the regular-pair kernels.  A target's sums depend on its own point only: thread t
+// always takes the same triangles in the same order and every reduction runs per
+// target, so a line's result does not depend on which lines share its rounds.
 //
 // Events (branch of alpha_eff at |E| = E0, |x| = r_max, entering another electrode)
 // are located on the re-stepped RK4 step by the Illinois variant of regula falsi
 // (at most 100 iterations); a step holds at most 4 events, the whole line at most
-// max_steps steps, so every loop is bounded.
+// max_steps steps, so every loop is bounded.  Warps synchronise only through CTA
+// barriers that every warp reaches once per round (a warp without a line joins
+// the rounds until no warp has one), so nothing waits on another CTA.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 
 #include "bem_internal.cuh"
 
 namespace tcore {
 
-constexpr int kT = 256;
+constexpr int kT = 256;          // threads of the adjoint's CTA-wide passes
 constexpr int kWarps = kT / 32;
+constexpr int kLW = 4;           // lines in flight per tracer CTA, one per warp
+constexpr int kLT = 32 * kLW;    // threads per tracer CTA
 
 struct TArgs {
     int64_t np;
@@ -38,34 +47,70 @@ struct TArgs {
     double h, r_max, c, E0, d, e_floor;
     int64_t max_steps;
     const float4* nrm32;  // [np] FP32 normal, region index in the bits of w
+    const float* u32;     // [np] u rounded to FP32 (the regular pairs' density)
 };
 
-// The FP32 field evaluation streams the triangles through shared memory in chunks
-// of TC (nodes, classification header, normal + region, density), double-buffered
-// with asynchronous copies so the loads of chunk c+1 overlap the work on chunk c.
-// Thread t takes triangle c*TC + t of every chunk: with TC = kT that is the
-// triangle sequence t, t + kT, t + 2 kT, ... of a plain strided loop.
+
+struct V4 {
+    double x, y, z, w;  // field (x,y,z) and the electrode indicator (w)
+};
+
+__device__ __forceinline__ double wsum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float wsumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// barrier of the kLT threads of a tracer CTA (its own id: warps reach it from
+// different places of the integrator)
+__device__ __forceinline__ void cta_bar() { asm volatile("bar.sync 1, %0;\n" ::"n"(kLT) : "memory"); }
+
+constexpr int kNearCap = 32;     // near pairs a (warp, target) list holds before it is evaluated
+
+// One round's requests and per-warp partial sums, in shared memory.
+struct Round {
+    double x[kLW][3];     // point posted by warp w
+    int sr[kLW];          // its seed region (triangles of other electrodes feed the indicator)
+    int act[kLW];         // 1 if warp w posted a point
+    float F[kLW][kLW][4];   // [target][warp] FP32 regular pairs (times 4 pi)
+    double N[kLW][kLW][4];  // [target][warp] closed-form pairs
+    double G[kLW][kLW][4];  // [target][warp] FP64 regular pairs (times 4 pi)
+    int32_t near[kLW][kLW][kNearCap];  // [warp][target slot] triangles of near pairs found
+};
+
+// The FP32 evaluation streams the triangles through shared memory in chunks of TC
+// (nodes, classification header, normal + region, density), double-buffered with
+// asynchronous copies so the loads of chunk c+1 overlap the work on chunk c.
 template <int Q>
 struct Stage32 {
-    static constexpr int TC = Q <= 16 ? kT : kT / 2;  // larger rules: half chunks fit the 227 KB
+    static constexpr int TC = Q <= 16 ? kLT : kLT / 2;  // larger rules: half chunks
     float4 node[2][TC * Q];
     float4 hdr[2][TC];
     float4 nrm[2][TC];
-    double u[2][TC];
+    float u[2][TC];
 };
 
-// dynamic shared memory a kernel running trace_line<F32, Q> must be launched with
+// dynamic shared memory a tracer kernel for (F32, Q) must be launched with
 template <bool F32, int Q>
 constexpr size_t field_smem()
 {
     return F32 ? sizeof(Stage32<Q>) : 0;
 }
 
-// allow a kernel more than the default 48 KB of dynamic shared memory
+// let a kernel take `bytes` of dynamic shared memory on top of its static shared
+// memory (past 48 KB in total the kernel must opt in)
 template <class Kernel>
 inline cudaError_t allow_smem(Kernel k, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes == 0) return cudaSuccess;
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -73,12 +118,6 @@ __device__ __forceinline__ void cp_async16(void* s, const void* g)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
-}
-
-__device__ __forceinline__ void cp_async8(void* s, const void* g)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -94,63 +133,69 @@ template <int Q>
 __device__ __forceinline__ void stage_chunk(const TArgs& A, Stage32<Q>& S, int b, int64_t c0, int n)
 {
     const float4* gn = A.node32 + c0 * Q;
-    for (int k = threadIdx.x; k < n * Q; k += kT) cp_async16(&S.node[b][k], gn + k);
-    for (int k = threadIdx.x; k < n; k += kT) {
+    for (int k = threadIdx.x; k < n * Q; k += kLT) cp_async16(&S.node[b][k], gn + k);
+    for (int k = threadIdx.x; k < n; k += kLT) {
         cp_async16(&S.hdr[b][k], A.hdr32 + c0 + k);
         cp_async16(&S.nrm[b][k], A.nrm32 + c0 + k);
-        cp_async8(&S.u[b][k], A.u + c0 + k);
     }
+    for (int k = threadIdx.x; k < n / 4; k += kLT) cp_async16(&S.u[b][4 * k], A.u32 + c0 + 4 * k);
+    for (int k = (n / 4) * 4 + threadIdx.x; k < n; k += kLT) S.u[b][k] = A.u32[c0 + k];
 }
 
-struct V4 {
-    double x, y, z, w;  // field (x,y,z) and the electrode indicator (w)
-};
-
-__device__ __forceinline__ double wsum(double v)
+// The field at NT posted points (targets tk[0..NT-1], the posting warps in order):
+// E(x) and the indicator sum_{j in other electrodes} G_j(x).n_j, as per-warp partial
+// sums in R (all threads call this).
+//  * FP32 form: regular pairs from the staged chunks, every node applied to all NT
+//    targets (independent chains, no branch between targets); near pairs are only
+//    listed during the sweep -- per warp and per target, in the order found -- and
+//    evaluated 32 at a time with the FP64 closed form by all lanes of the warp, so
+//    the slow FP64 units are busy with full warps instead of one lane at a time.
+//  * FP64 form: a plain strided loop, FP64 regular pairs, closed form in place.
+template <bool F32, int Q, int NT>
+__device__ void eval_targets(const TArgs& A, Round& R, unsigned amask)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// sum over the CTA in a fixed order; every thread gets the same result
-__device__ inline V4 block_sum(V4 v, double* sh)
-{
-    v.x = wsum(v.x); v.y = wsum(v.y); v.z = wsum(v.z); v.w = wsum(v.w);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) {
-        sh[warp] = v.x; sh[kWarps + warp] = v.y; sh[2 * kWarps + warp] = v.z; sh[3 * kWarps + warp] = v.w;
-    }
-    __syncthreads();
-    V4 r = {0.0, 0.0, 0.0, 0.0};
+    int tk[NT], sr[NT];
+    float xf[NT], yf[NT], zf[NT];
+    float fx[NT], fy[NT], fz[NT], fi[NT];      // FP32 regular pairs (times 4 pi)
+    double nx[NT], ny[NT], nz[NT], ni[NT];     // closed-form pairs
+    double qx[NT], qy[NT], qz[NT], qi[NT];     // FP64 regular pairs (times 4 pi)
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        r.x += sh[w]; r.y += sh[kWarps + w]; r.z += sh[2 * kWarps + w]; r.w += sh[3 * kWarps + w];
+    for (int s = 0; s < NT; ++s) {
+        tk[s] = (int)__fns(amask, 0, s + 1);
+        sr[s] = R.sr[tk[s]];
+        xf[s] = __double2float_rn(R.x[tk[s]][0]);
+        yf[s] = __double2float_rn(R.x[tk[s]][1]);
+        zf[s] = __double2float_rn(R.x[tk[s]][2]);
+        fx[s] = fy[s] = fz[s] = fi[s] = 0.f;
+        nx[s] = ny[s] = nz[s] = ni[s] = 0.0;
+        qx[s] = qy[s] = qz[s] = qi[s] = 0.0;
     }
-    return r;
-}
-
-// E(x) and the indicator sum_{j in other electrodes} G_j(x).n_j
-template <bool F32, int Q>
-__device__ __noinline__ V4 cta_field(const TArgs& A, const double* x, int seed_region, double* sh)
-{
-    const float xf = __double2float_rn(x[0]), yf = __double2float_rn(x[1]), zf = __double2float_rn(x[2]);
-    float fx = 0.f, fy = 0.f, fz = 0.f, fi = 0.f;      // FP32 regular pairs (times 4 pi)
-    double qx = 0.0, qy = 0.0, qz = 0.0, qi = 0.0;     // FP64 regular pairs (times 4 pi)
-    double nx_ = 0.0, ny_ = 0.0, nz_ = 0.0, ni = 0.0;  // closed-form pairs
-    // a near pair: the closed form in FP64
-    auto near_pair = [&](int64_t j, double uj, bool mark) {
+    // a near pair of target slot s: the closed form in FP64
+    auto near_pair = [&](int s, int64_t j, double uj, bool mark) {
         const double* gp = A.geo + GEO_STRIDE * j;
         double S, Gx, Gy, Gz;
-        tri_closed_form(gp, x[0], x[1], x[2], false, S, Gx, Gy, Gz);
-        nx_ = fma(uj, Gx, nx_); ny_ = fma(uj, Gy, ny_); nz_ = fma(uj, Gz, nz_);
-        if (mark) ni += Gx * gp[GEO_N] + Gy * gp[GEO_N + 1] + Gz * gp[GEO_N + 2];
+        tri_closed_form(gp, R.x[tk[s]][0], R.x[tk[s]][1], R.x[tk[s]][2], false, S, Gx, Gy, Gz);
+        nx[s] = fma(uj, Gx, nx[s]); ny[s] = fma(uj, Gy, ny[s]); nz[s] = fma(uj, Gz, nz[s]);
+        if (mark) ni[s] += Gx * gp[GEO_N] + Gy * gp[GEO_N + 1] + Gz * gp[GEO_N + 2];
     };
     if constexpr (F32) {
         extern __shared__ __align__(16) unsigned char tcore_dyn[];
         Stage32<Q>& S = *reinterpret_cast<Stage32<Q>*>(tcore_dyn);
         constexpr int TC = Stage32<Q>::TC;
+        int ncnt[NT];  // entries in this warp's list of each target (warp-uniform)
+#pragma unroll
+        for (int s = 0; s < NT; ++s) ncnt[s] = 0;
+        // evaluate the listed near pairs of slot s: lane i takes entry i
+        auto flush = [&](int s) {
+            if (lane < ncnt[s]) {
+                const int32_t j = R.near[warp][s][lane];
+                const int rj = A.region[j];
+                near_pair(s, j, A.u[j], A.electrode[rj] != 0 && rj != sr[s]);
+            }
+            __syncwarp();
+            ncnt[s] = 0;
+        };
         const int64_t nch = (A.np + TC - 1) / TC;
         const int t = threadIdx.x;
         stage_chunk<Q>(A, S, 0, 0, (int)min((int64_t)TC, A.np));
@@ -165,61 +210,171 @@ __device__ __noinline__ V4 cta_field(const TArgs& A, const double* x, int seed_r
             } else {
                 cp_async_wait<0>();
             }
-            __syncthreads();
+            cta_bar();
             const int64_t j = c * TC + t;
-            if (t < TC && j < A.np) {
+            const bool valid = t < TC && j < A.np;
+            bool nearf[NT];
+            if (valid) {
                 const float4 nv = S.nrm[b][t];
+                const float4 h = S.hdr[b][t];
                 const int rj = __float_as_int(nv.w);
-                const bool mark = rj != seed_region && A.electrode[rj] != 0;
-                const double uj = S.u[b][t];
-                if (is_far32(xf, yf, zf, S.hdr[b][t])) {
-                    float gx = 0.f, gy = 0.f, gz = 0.f;
+                const bool elec = A.electrode[rj] != 0;
+                const float uf = S.u[b][t];
+                float gx[NT], gy[NT], gz[NT];
 #pragma unroll
-                    for (int k = 0; k < Q; ++k) {
-                        const float4 nd = S.node[b][t * Q + k];
-                        const float dx = xf - nd.x, dy = yf - nd.y, dz = zf - nd.z;
+                for (int s = 0; s < NT; ++s) gx[s] = gy[s] = gz[s] = 0.f;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float4 nd = S.node[b][t * Q + q];
+#pragma unroll
+                    for (int s = 0; s < NT; ++s) {
+                        const float dx = xf[s] - nd.x, dy = yf[s] - nd.y, dz = zf[s] - nd.z;
                         const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f))));
                         const float t3 = nd.w * ri * ri * ri;
-                        gx = fmaf(t3, dx, gx); gy = fmaf(t3, dy, gy); gz = fmaf(t3, dz, gz);
+                        gx[s] = fmaf(t3, dx, gx[s]); gy[s] = fmaf(t3, dy, gy[s]); gz[s] = fmaf(t3, dz, gz[s]);
                     }
-                    const float uf = __double2float_rn(uj);
-                    fx = fmaf(uf, gx, fx); fy = fmaf(uf, gy, fy); fz = fmaf(uf, gz, fz);
-                    if (mark) fi += gx * nv.x + gy * nv.y + gz * nv.z;
-                } else {
-                    near_pair(j, uj, mark);
                 }
-            }
-            __syncthreads();  // buffer b is refilled in the next iteration
-        }
-    } else {
-        for (int64_t j = threadIdx.x; j < A.np; j += kT) {
-            const int rj = A.region[j];
-            const bool mark = rj != seed_region && A.electrode[rj] != 0;
-            const double uj = A.u[j];
-            if (is_far64(x[0], x[1], x[2], A.hdr64[j])) {
-                const double* gp = A.geo + GEO_STRIDE * j;
-                double gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const double4 nd = A.node64[j * Q + k];
-                    const double dx = x[0] - nd.x, dy = x[1] - nd.y, dz = x[2] - nd.z;
-                    const double ri = rsqrt(fma(dx, dx, fma(dy, dy, fma(dz, dz, 1e-200))));
-                    const double t3 = nd.w * ri * ri * ri;
-                    gx = fma(t3, dx, gx); gy = fma(t3, dy, gy); gz = fma(t3, dz, gz);
+                for (int s = 0; s < NT; ++s) {
+                    const bool far = is_far32(xf[s], yf[s], zf[s], h);
+                    nearf[s] = !far;
+                    const float m = far ? uf : 0.f;
+                    fx[s] = fmaf(m, gx[s], fx[s]); fy[s] = fmaf(m, gy[s], fy[s]); fz[s] = fmaf(m, gz[s], fz[s]);
+                    if (far && elec && rj != sr[s]) fi[s] += gx[s] * nv.x + gy[s] * nv.y + gz[s] * nv.z;
                 }
-                qx = fma(uj, gx, qx); qy = fma(uj, gy, qy); qz = fma(uj, gz, qz);
-                if (mark) qi += gx * gp[GEO_N] + gy * gp[GEO_N + 1] + gz * gp[GEO_N + 2];
             } else {
-                near_pair(j, uj, mark);
+#pragma unroll
+                for (int s = 0; s < NT; ++s) nearf[s] = false;
+            }
+            // list the near pairs (the warp is converged here)
+#pragma unroll
+            for (int s = 0; s < NT; ++s) {
+                const unsigned bal = __ballot_sync(0xffffffffu, nearf[s]);
+                if (bal == 0u) continue;
+                const int cnt = __popc(bal);
+                if (ncnt[s] + cnt > kNearCap) flush(s);
+                if (nearf[s]) R.near[warp][s][ncnt[s] + __popc(bal & ((1u << lane) - 1u))] = (int32_t)j;
+                __syncwarp();
+                ncnt[s] += cnt;
+            }
+            cta_bar();  // buffer b is refilled in the next iteration
+        }
+#pragma unroll
+        for (int s = 0; s < NT; ++s)
+            if (ncnt[s] > 0) flush(s);
+    } else {
+        for (int64_t j = threadIdx.x; j < A.np; j += kLT) {
+            const int rj = A.region[j];
+            const bool elec = A.electrode[rj] != 0;
+            const double uj = A.u[j];
+            const double4 h = A.hdr64[j];
+            const double* gp = A.geo + GEO_STRIDE * j;
+#pragma unroll
+            for (int s = 0; s < NT; ++s) {
+                const double* xs = R.x[tk[s]];
+                const bool mark = elec && rj != sr[s];
+                if (is_far64(xs[0], xs[1], xs[2], h)) {
+                    double gx = 0.0, gy = 0.0, gz = 0.0;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const double4 nd = A.node64[j * Q + q];
+                        const double dx = xs[0] - nd.x, dy = xs[1] - nd.y, dz = xs[2] - nd.z;
+                        const double ri = rsqrt(fma(dx, dx, fma(dy, dy, fma(dz, dz, 1e-200))));
+                        const double t3 = nd.w * ri * ri * ri;
+                        gx = fma(t3, dx, gx); gy = fma(t3, dy, gy); gz = fma(t3, dz, gz);
+                    }
+                    qx[s] = fma(uj, gx, qx[s]); qy[s] = fma(uj, gy, qy[s]); qz[s] = fma(uj, gz, qz[s]);
+                    if (mark) qi[s] += gx * gp[GEO_N] + gy * gp[GEO_N + 1] + gz * gp[GEO_N + 2];
+                } else {
+                    near_pair(s, j, uj, mark);
+                }
             }
         }
     }
-    V4 v;
-    v.x = nx_ + kInv4Pi * (qx + (double)fx);
-    v.y = ny_ + kInv4Pi * (qy + (double)fy);
-    v.z = nz_ + kInv4Pi * (qz + (double)fz);
-    v.w = ni + kInv4Pi * (qi + (double)fi);
-    return block_sum(v, sh);
+    // per-target warp sums (fixed butterfly order), lane 0 stores them
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        const float a = wsumf(fx[s]), bb = wsumf(fy[s]), cc = wsumf(fz[s]), dd = wsumf(fi[s]);
+        double e0 = nx[s], e1 = ny[s], e2 = nz[s], e3 = ni[s];
+        if (__any_sync(0xffffffffu, e0 != 0.0 || e1 != 0.0 || e2 != 0.0 || e3 != 0.0)) {
+            e0 = wsum(e0); e1 = wsum(e1); e2 = wsum(e2); e3 = wsum(e3);
+        }
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+        if constexpr (!F32) {
+            g0 = wsum(qx[s]); g1 = wsum(qy[s]); g2 = wsum(qz[s]); g3 = wsum(qi[s]);
+        }
+        if (lane == 0) {
+            const int k = tk[s];
+            R.F[k][warp][0] = a; R.F[k][warp][1] = bb; R.F[k][warp][2] = cc; R.F[k][warp][3] = dd;
+            R.N[k][warp][0] = e0; R.N[k][warp][1] = e1; R.N[k][warp][2] = e2; R.N[k][warp][3] = e3;
+            R.G[k][warp][0] = g0; R.G[k][warp][1] = g1; R.G[k][warp][2] = g2; R.G[k][warp][3] = g3;
+        }
+    }
+}
+
+// The field at every posted point (all threads call this after the round's entry
+// barrier): the variant for the number of posting warps.
+template <bool F32, int Q>
+__device__ __noinline__ void eval_round(const TArgs& A, Round& R)
+{
+    unsigned amask = 0u;
+#pragma unroll
+    for (int k = 0; k < kLW; ++k)
+        if (R.act[k]) amask |= 1u << k;
+    switch (__popc(amask)) {
+        case 1: eval_targets<F32, Q, 1>(A, R, amask); break;
+        case 2: eval_targets<F32, Q, 2>(A, R, amask); break;
+        case 3: eval_targets<F32, Q, 3>(A, R, amask); break;
+        case 4: eval_targets<F32, Q, 4>(A, R, amask); break;
+        default: break;
+    }
+}
+
+// the field at warp w's point from the round's partial sums (fixed order)
+__device__ __forceinline__ V4 round_result(const Round& R, int w)
+{
+    double f[4] = {0.0, 0.0, 0.0, 0.0}, n[4] = {0.0, 0.0, 0.0, 0.0}, g[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int v = 0; v < kLW; ++v)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            f[c] += (double)R.F[w][v][c];
+            n[c] += R.N[w][v][c];
+            g[c] += R.G[w][v][c];
+        }
+    return V4{n[0] + kInv4Pi * (g[0] + f[0]), n[1] + kInv4Pi * (g[1] + f[1]),
+              n[2] + kInv4Pi * (g[2] + f[2]), n[3] + kInv4Pi * (g[3] + f[3])};
+}
+
+// The calling warp's field at x (all 32 lanes call this with the same x): one round.
+template <bool F32, int Q>
+__device__ V4 field(const TArgs& A, Round& R, const double* x, int seed_region)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        R.x[w][0] = x[0]; R.x[w][1] = x[1]; R.x[w][2] = x[2];
+        R.sr[w] = seed_region;
+        R.act[w] = 1;
+    }
+    cta_bar();
+    eval_round<F32, Q>(A, R);
+    cta_bar();
+    return round_result(R, w);
+}
+
+// A round in which the calling warp posts nothing; false if no warp posted a point
+// (then every warp of the CTA returns false from the same round).
+template <bool F32, int Q>
+__device__ bool idle_round(const TArgs& A, Round& R)
+{
+    if ((threadIdx.x & 31) == 0) R.act[threadIdx.x >> 5] = 0;
+    cta_bar();
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kLW; ++k) any = any || R.act[k] != 0;
+    if (any) eval_round<F32, Q>(A, R);
+    cta_bar();
+    return any;
 }
 
 __device__ __forceinline__ double norm3(double a, double b, double c) { return sqrt(a * a + b * b + c * c); }
@@ -231,12 +386,12 @@ __device__ __forceinline__ double alpha_eff(const TArgs& A, double Em, int side)
 
 // one RK4 step of length s from (x, K); E0c: field at x if known
 template <bool F32, int Q>
-__device__ void rk4(const TArgs& A, int seed_region, double s0, int side, const double* x, double K,
-                    double s, const V4* E0c, double* x1, double& K1, double* sh)
+__device__ void rk4(const TArgs& A, Round& R, int seed_region, double s0, int side, const double* x,
+                    double K, double s, const V4* E0c, double* x1, double& K1)
 {
     double k[4][3], a[4], y[3] = {x[0], x[1], x[2]};
     for (int st = 0; st < 4; ++st) {
-        const V4 E = (st == 0 && E0c) ? *E0c : cta_field<F32, Q>(A, y, seed_region, sh);
+        const V4 E = (st == 0 && E0c) ? *E0c : field<F32, Q>(A, R, y, seed_region);
         const double Em = norm3(E.x, E.y, E.z);
         k[st][0] = E.x * (s0 / Em);
         k[st][1] = E.y * (s0 / Em);
@@ -255,26 +410,26 @@ __device__ void rk4(const TArgs& A, int seed_region, double s0, int side, const 
 enum { EV_ALPHA = 0, EV_RMAX = 1, EV_ELECTRODE = 2 };
 
 template <bool F32, int Q>
-__device__ double event_g(const TArgs& A, int seed_region, double s0, int side, const double* x,
-                          double K, const V4* E0c, double sig, int ev, double* sh)
+__device__ double event_g(const TArgs& A, Round& R, int seed_region, double s0, int side, const double* x,
+                          double K, const V4* E0c, double sig, int ev)
 {
     double x1[3], K1;
-    rk4<F32, Q>(A, seed_region, s0, side, x, K, sig, E0c, x1, K1, sh);
+    rk4<F32, Q>(A, R, seed_region, s0, side, x, K, sig, E0c, x1, K1);
     if (ev == EV_RMAX) return norm3(x1[0], x1[1], x1[2]) - A.r_max;
-    const V4 E = cta_field<F32, Q>(A, x1, seed_region, sh);
+    const V4 E = field<F32, Q>(A, R, x1, seed_region);
     if (ev == EV_ALPHA) return norm3(E.x, E.y, E.z) - A.E0;
     return E.w + 0.5;
 }
 
 template <bool F32, int Q>
-__device__ double illinois(const TArgs& A, int seed_region, double s0, int side, const double* x,
-                           double K, const V4* E0c, double b, double ga, double gb, int ev, double* sh)
+__device__ double illinois(const TArgs& A, Round& R, int seed_region, double s0, int side, const double* x,
+                           double K, const V4* E0c, double b, double ga, double gb, int ev)
 {
     double a = 0.0, c = b;
     int last = 0;
     for (int it = 0; it < 100; ++it) {
         c = (ga * b - gb * a) / (ga - gb);
-        const double gc = event_g<F32, Q>(A, seed_region, s0, side, x, K, E0c, c, ev, sh);
+        const double gc = event_g<F32, Q>(A, R, seed_region, s0, side, x, K, E0c, c, ev);
         if (gc == 0.0) break;
         if ((gc > 0.0) == (gb > 0.0)) {
             b = c; gb = gc;
@@ -300,18 +455,19 @@ struct NoRec {
     __device__ void sub(int64_t step, int k, double sig, int kind) {}
 };
 
-// Trace one line from seed xs; all threads of the CTA call this with the same
-// arguments.  Outputs (K, status, steps, end point) are returned to every thread.
+// Trace one line from seed xs; the 32 lanes of one warp call this with the same
+// arguments while the other warps of the CTA trace their own lines or idle.  The
+// outputs (K, status, steps, end point) are returned to every lane.
 template <bool F32, int Q, class Rec>
-__device__ void trace_line(const TArgs& A, const double* xs, Rec& rec, double& K_out, int& st_out,
-                           int64_t& ns_out, double* xe_out, double* sh, double* s_bd, long long* s_bj)
+__device__ void trace_line(const TArgs& A, Round& R, const double* xs, Rec& rec, double& K_out,
+                           int& st_out, int64_t& ns_out, double* xe_out)
 {
     double x[3] = {xs[0], xs[1], xs[2]};
     double K = 0.0;
     // electrode of the seed: the triangle with the nearest centroid (first on ties)
     double bd = 1e300;
     long long bj = 0;
-    for (int64_t j = threadIdx.x; j < A.np; j += kT) {
+    for (int64_t j = threadIdx.x & 31; j < A.np; j += 32) {
         const double* c = A.geo + GEO_STRIDE * j + GEO_CTR;
         const double dd = (x[0] - c[0]) * (x[0] - c[0]) + (x[1] - c[1]) * (x[1] - c[1]) + (x[2] - c[2]) * (x[2] - c[2]);
         if (dd < bd) { bd = dd; bj = j; }
@@ -322,15 +478,9 @@ __device__ void trace_line(const TArgs& A, const double* xs, Rec& rec, double& K
         const long long oj = __shfl_xor_sync(0xffffffffu, bj, o);
         if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
     }
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) { s_bd[threadIdx.x >> 5] = bd; s_bj[threadIdx.x >> 5] = bj; }
-    __syncthreads();
-    bd = s_bd[0]; bj = s_bj[0];
-    for (int w = 1; w < kWarps; ++w)
-        if (s_bd[w] < bd || (s_bd[w] == bd && s_bj[w] < bj)) { bd = s_bd[w]; bj = s_bj[w]; }
     const int seed_region = A.region[bj];
     const double* nb = A.geo + GEO_STRIDE * bj + GEO_N;
-    V4 E = cta_field<F32, Q>(A, x, -2, sh);
+    V4 E = field<F32, Q>(A, R, x, -2);
     const double s0 = (E.x * nb[0] + E.y * nb[1] + E.z * nb[2]) >= 0.0 ? 1.0 : -1.0;
     int side = norm3(E.x, E.y, E.z) > A.E0 ? 1 : -1;
     rec.begin(s0, seed_region);
@@ -338,7 +488,7 @@ __device__ void trace_line(const TArgs& A, const double* xs, Rec& rec, double& K
     int64_t step = 0;
     bool have = false;  // E holds the field at x (with the seed's indicator)
     for (; step < A.max_steps; ++step) {
-        if (!have) E = cta_field<F32, Q>(A, x, seed_region, sh);
+        if (!have) E = field<F32, Q>(A, R, x, seed_region);
         have = false;
         const double Em = norm3(E.x, E.y, E.z);
         if (!isfinite(Em)) { st = -1; break; }
@@ -349,25 +499,25 @@ __device__ void trace_line(const TArgs& A, const double* xs, Rec& rec, double& K
         for (int nev = 0; rem > 0.0 && nev < 4; ++nev) {
             const V4* Ec = first ? &E : nullptr;
             double x1[3], K1;
-            rk4<F32, Q>(A, seed_region, s0, side, x, K, rem, Ec, x1, K1, sh);
-            const V4 E1 = cta_field<F32, Q>(A, x1, seed_region, sh);
+            rk4<F32, Q>(A, R, seed_region, s0, side, x, K, rem, Ec, x1, K1);
+            const V4 E1 = field<F32, Q>(A, R, x1, seed_region);
             const double E1m = norm3(E1.x, E1.y, E1.z);
             double best = 2.0 * rem;
             int which = -1;
             if ((E1m > A.E0) != (side > 0)) {
-                const double ga = event_g<F32, Q>(A, seed_region, s0, side, x, K, Ec, 0.0, EV_ALPHA, sh);
-                const double sg = illinois<F32, Q>(A, seed_region, s0, side, x, K, Ec, rem, ga, E1m - A.E0, EV_ALPHA, sh);
+                const double ga = event_g<F32, Q>(A, R, seed_region, s0, side, x, K, Ec, 0.0, EV_ALPHA);
+                const double sg = illinois<F32, Q>(A, R, seed_region, s0, side, x, K, Ec, rem, ga, E1m - A.E0, EV_ALPHA);
                 if (sg < best) { best = sg; which = EV_ALPHA; }
             }
             const double r1 = norm3(x1[0], x1[1], x1[2]);
             if (r1 >= A.r_max) {
-                const double sg = illinois<F32, Q>(A, seed_region, s0, side, x, K, Ec, rem,
-                                                   norm3(x[0], x[1], x[2]) - A.r_max, r1 - A.r_max, EV_RMAX, sh);
+                const double sg = illinois<F32, Q>(A, R, seed_region, s0, side, x, K, Ec, rem,
+                                                   norm3(x[0], x[1], x[2]) - A.r_max, r1 - A.r_max, EV_RMAX);
                 if (sg < best) { best = sg; which = EV_RMAX; }
             }
             if (E1.w < -0.5) {
-                const double ga = event_g<F32, Q>(A, seed_region, s0, side, x, K, Ec, 0.0, EV_ELECTRODE, sh);
-                const double sg = illinois<F32, Q>(A, seed_region, s0, side, x, K, Ec, rem, ga, E1.w + 0.5, EV_ELECTRODE, sh);
+                const double ga = event_g<F32, Q>(A, R, seed_region, s0, side, x, K, Ec, 0.0, EV_ELECTRODE);
+                const double sg = illinois<F32, Q>(A, R, seed_region, s0, side, x, K, Ec, rem, ga, E1.w + 0.5, EV_ELECTRODE);
                 if (sg < best) { best = sg; which = EV_ELECTRODE; }
             }
             if (which < 0) {
@@ -381,7 +531,7 @@ __device__ void trace_line(const TArgs& A, const double* xs, Rec& rec, double& K
             }
             rec.sub(step, nev, best, which == EV_ALPHA ? SUB_ALPHA : (which == EV_RMAX ? SUB_RMAX : SUB_ELECTRODE));
             double xn[3], Kn;
-            rk4<F32, Q>(A, seed_region, s0, side, x, K, best, Ec, xn, Kn, sh);
+            rk4<F32, Q>(A, R, seed_region, s0, side, x, K, best, Ec, xn, Kn);
             x[0] = xn[0]; x[1] = xn[1]; x[2] = xn[2];
             K = Kn;
             first = false;
@@ -400,6 +550,64 @@ __device__ void trace_line(const TArgs& A, const double* xs, Rec& rec, double& K
     st_out = st;
     ns_out = step;
     xe_out[0] = x[0]; xe_out[1] = x[1]; xe_out[2] = x[2];
+}
+
+// Persistent driver: the warps of a tracer CTA take lines of the CTA's current mesh
+// from that mesh's counter (next[i], lines 0..L(i)-1) and trace them with
+// line_fn(A, R, mesh, line); a warp without a line joins the rounds of the others.
+// When every warp has run out, the CTA moves to another mesh with lines left.  The
+// counters only grow, so the loops end once all counters have passed their L.
+// args(i) gives mesh i's TArgs, L(i) its line count.
+template <bool F32, int Q, class ArgsFn, class CountFn, class LineFn>
+__device__ void run_lines(ArgsFn args, CountFn L, int ninst, unsigned long long* next, TArgs& sA, Round& R,
+                          int& s_inst, LineFn line_fn)
+{
+    const int lane = threadIdx.x & 31;
+    int start = (int)(blockIdx.x % (unsigned)ninst);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int pick = -1;
+            for (int k = 0; k < ninst; ++k) {
+                const int i = (start + k) % ninst;
+                if (*(volatile unsigned long long*)&next[i] < (unsigned long long)L(i)) {
+                    pick = i;
+                    break;
+                }
+            }
+            s_inst = pick;
+            if (pick >= 0) sA = args(pick);
+        }
+        cta_bar();
+        const int ci = s_inst;
+        if (ci < 0) break;
+        const unsigned long long Lc = (unsigned long long)L(ci);
+        for (;;) {
+            unsigned long long l = 0;
+            if (lane == 0) l = atomicAdd(&next[ci], 1ull);
+            l = __shfl_sync(0xffffffffu, l, 0);
+            if (l >= Lc) break;
+            line_fn(sA, R, ci, (int64_t)l);
+        }
+        while (idle_round<F32, Q>(sA, R)) {
+        }
+        start = ci;
+        cta_bar();  // sA and s_inst are rewritten next
+    }
+}
+
+// persistent grid of a tracer kernel: one CTA per SM at least, up to the resident
+// limit, never more CTAs than lines
+template <class Kernel>
+inline unsigned lines_grid(Kernel k, size_t smem, int num_sms, int64_t lines)
+{
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kLT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int64_t cap = (int64_t)num_sms * std::max(per_sm, 1);
+    const int64_t want = std::max<int64_t>((lines + kLW - 1) / kLW, num_sms);
+    return (unsigned)std::max<int64_t>(1, std::min(std::min(want, cap), lines));
 }
 
 }  // namespace tcore

@@ -113,6 +113,21 @@ def test_matvec_df_reproduces_fp64(case, bem):
     assert np.abs(ydf - y64).max() / np.abs(y64).max() < 1e-12
 
 
+@pytest.mark.parametrize("nr", [2, 3, 4])
+def test_matvec_df_multi_rhs(case, bem, nr):
+    """Several right-hand sides in one double-FP32 pass: each equals its own
+    single-right-hand-side pass bit for bit, and the oracle's FP64 product to rounding
+    (1e-11, the FP64 form's bound)."""
+    name, mesh, ctx, P, A = case
+    X = np.random.default_rng(40 + nr).normal(size=(nr, ctx.nunk))
+    Y = ctx.matvec(torch.tensor(X), precision=bem.DF)
+    for r in range(nr):
+        y1 = ctx.matvec(torch.tensor(X[r]), precision=bem.DF)
+        assert torch.equal(Y[r], y1)
+        ref = A @ X[r]
+        assert np.abs(Y[r].cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-11
+
+
 @pytest.mark.parametrize("residual", [0, 1])
 def test_mixed_solve_residual_modes(case, bem, residual):
     """BEM_MIXED with the refinement residual in double-FP32 (default) or FP64:
