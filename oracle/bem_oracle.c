@@ -429,10 +429,16 @@ static double event_g(const fsrc* F, const tparams* P, int seed_region, double s
     return ind + 0.5;
 }
 
-/* Illinois regula falsi on [0, b] where g(0) = ga and g(b) = gb differ in sign */
+/* Illinois regula falsi on [0, b] where g(0) = ga and g(b) = gb differ in sign.
+ * The event is tested at the end of the step (g(b) on the far side, or zero: a root
+ * at b); if g(0) is already on that side (or zero) there is no crossing inside the
+ * step -- the event condition held where the sub-step starts -- and the event is
+ * located at 0. */
 static double illinois(const fsrc* F, const tparams* P, int seed_region, double s0, int side, vec x,
                        double K, double b, double ga, double gb, int ev)
 {
+    if (gb == 0.0) return b;
+    if (ga == 0.0 || (ga > 0.0) == (gb > 0.0)) return 0.0;
     double a = 0.0, c = b;
     int last = 0;
     for (int it = 0; it < 100; ++it) {

@@ -84,8 +84,8 @@ k_adj_forward(TArgs A, const double* __restrict__ seeds, int64_t L, unsigned lon
 {
     __shared__ Round R;
     __shared__ TArgs sA;
-    __shared__ int s_inst;
-    run_lines<F32, Q>([&](int) { return A; }, [&](int) { return L; }, 1, next, sA, R, s_inst,
+    __shared__ int s_int[3];
+    run_lines<F32, Q>([&](int) { return A; }, [&](int) { return L; }, 1, L, next, sA, R, s_int,
                       [&](const TArgs& a, Round& r, int, int64_t line) {
                           TapeRec rec{tape ? tape + off[line] : nullptr, tape ? cap[line] : 0, 0, 1.0, -1};
                           double K, xe[3];

@@ -560,9 +560,10 @@ k_btrace(const tcore::TArgs* __restrict__ args, const int64_t* __restrict__ loff
 {
     __shared__ tcore::Round R;
     __shared__ tcore::TArgs sA;
-    __shared__ int s_inst;
+    __shared__ int s_int[3];
     tcore::run_lines<F32, Q>(
-        [&](int i) { return args[i]; }, [&](int i) { return loff[i + 1] - loff[i]; }, ninst, next, sA, R, s_inst,
+        [&](int i) { return args[i]; }, [&](int i) { return loff[i + 1] - loff[i]; }, ninst, loff[ninst], next, sA,
+        R, s_int,
         [&](const tcore::TArgs& a, tcore::Round& r, int i, int64_t l) {
             tcore::NoRec rec;
             double K, xe[3];

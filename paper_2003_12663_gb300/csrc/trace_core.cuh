@@ -31,7 +31,7 @@ namespace tcore {
 
 constexpr int kT = 256;          // threads of the adjoint's CTA-wide passes
 constexpr int kWarps = kT / 32;
-constexpr int kLW = 4;           // lines in flight per tracer CTA, one per warp
+constexpr int kLW = 8;           // lines in flight per tracer CTA, one per warp
 constexpr int kLT = 32 * kLW;    // threads per tracer CTA
 
 struct TArgs {
@@ -87,15 +87,17 @@ struct Round {
 };
 
 // The FP32 evaluation streams the triangles through shared memory in chunks of TC
-// (nodes, classification header, normal + region, density), double-buffered with
-// asynchronous copies so the loads of chunk c+1 overlap the work on chunk c.
+// (nodes, classification header, normal + region, density) with an NS-stage ring of
+// asynchronous copies: while chunk c is evaluated the copies of chunks c+1 .. c+NS-1
+// are in flight, so a round with a single posted point is not left waiting on L2.
 template <int Q>
 struct Stage32 {
     static constexpr int TC = Q <= 16 ? kLT : kLT / 2;  // larger rules: half chunks
-    float4 node[2][TC * Q];
-    float4 hdr[2][TC];
-    float4 nrm[2][TC];
-    float u[2][TC];
+    static constexpr int NS = Q <= 9 ? 4 : 2;           // stages (184 KB for Q = 9)
+    float4 node[NS][TC * Q];
+    float4 hdr[NS][TC];
+    float4 nrm[NS][TC];
+    float u[NS][TC];
 };
 
 // dynamic shared memory a tracer kernel for (F32, Q) must be launched with
@@ -142,74 +144,90 @@ __device__ __forceinline__ void stage_chunk(const TArgs& A, Stage32<Q>& S, int b
     for (int k = (n / 4) * 4 + threadIdx.x; k < n; k += kLT) S.u[b][k] = A.u32[c0 + k];
 }
 
-// The field at NT posted points (targets tk[0..NT-1], the posting warps in order):
-// E(x) and the indicator sum_{j in other electrodes} G_j(x).n_j, as per-warp partial
-// sums in R (all threads call this).
+// The field at the posted points (slots 0..nt-1: the posting warps in order; NT is
+// nt rounded up to a power of two, the extra slots repeat the last point and are not
+// stored): E(x) and the indicator sum_{j in other electrodes} G_j(x).n_j, as
+// per-warp partial sums in R (all threads call this).
 //  * FP32 form: regular pairs from the staged chunks, every node applied to all NT
-//    targets (independent chains, no branch between targets); near pairs are only
-//    listed during the sweep -- per warp and per target, in the order found -- and
+//    slots (independent chains, no branch between slots).  Near pairs are only
+//    listed during the sweep -- per warp and per slot, in the order found -- and
 //    evaluated 32 at a time with the FP64 closed form by all lanes of the warp, so
-//    the slow FP64 units are busy with full warps instead of one lane at a time.
-//  * FP64 form: a plain strided loop, FP64 regular pairs, closed form in place.
+//    the slow FP64 units are busy with full warps instead of one lane at a time;
+//    each batch is summed over the warp and added to R.N by lane 0.
+//  * FP64 form: one plain strided pass per slot, FP64 regular pairs, closed form in
+//    place.
 template <bool F32, int Q, int NT>
-__device__ void eval_targets(const TArgs& A, Round& R, unsigned amask)
+__device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int tk[NT], sr[NT];
-    float xf[NT], yf[NT], zf[NT];
-    float fx[NT], fy[NT], fz[NT], fi[NT];      // FP32 regular pairs (times 4 pi)
-    double nx[NT], ny[NT], nz[NT], ni[NT];     // closed-form pairs
-    double qx[NT], qy[NT], qz[NT], qi[NT];     // FP64 regular pairs (times 4 pi)
+    int tk[NT];
 #pragma unroll
-    for (int s = 0; s < NT; ++s) {
-        tk[s] = (int)__fns(amask, 0, s + 1);
-        sr[s] = R.sr[tk[s]];
-        xf[s] = __double2float_rn(R.x[tk[s]][0]);
-        yf[s] = __double2float_rn(R.x[tk[s]][1]);
-        zf[s] = __double2float_rn(R.x[tk[s]][2]);
-        fx[s] = fy[s] = fz[s] = fi[s] = 0.f;
-        nx[s] = ny[s] = nz[s] = ni[s] = 0.0;
-        qx[s] = qy[s] = qz[s] = qi[s] = 0.0;
-    }
-    // a near pair of target slot s: the closed form in FP64
-    auto near_pair = [&](int s, int64_t j, double uj, bool mark) {
+    for (int s = 0; s < NT; ++s) tk[s] = (int)__fns(amask, 0, min(s, nt - 1) + 1);
+    if (lane == 0)
+#pragma unroll
+        for (int s = 0; s < NT; ++s)
+            if (s < nt)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) R.N[tk[s]][warp][c] = 0.0;
+    __syncwarp();
+    // the closed form of near pair (slot s, triangle j); the contribution to E and to
+    // the indicator is added to d[0..3]
+    auto near_pair = [&](int s, int64_t j, double* d) {
         const double* gp = A.geo + GEO_STRIDE * j;
+        const int rj = A.region[j];
+        const bool mark = A.electrode[rj] != 0 && rj != R.sr[tk[s]];
+        const double uj = A.u[j];
         double S, Gx, Gy, Gz;
         tri_closed_form(gp, R.x[tk[s]][0], R.x[tk[s]][1], R.x[tk[s]][2], false, S, Gx, Gy, Gz);
-        nx[s] = fma(uj, Gx, nx[s]); ny[s] = fma(uj, Gy, ny[s]); nz[s] = fma(uj, Gz, nz[s]);
-        if (mark) ni[s] += Gx * gp[GEO_N] + Gy * gp[GEO_N + 1] + Gz * gp[GEO_N + 2];
+        d[0] = fma(uj, Gx, d[0]); d[1] = fma(uj, Gy, d[1]); d[2] = fma(uj, Gz, d[2]);
+        if (mark) d[3] += Gx * gp[GEO_N] + Gy * gp[GEO_N + 1] + Gz * gp[GEO_N + 2];
     };
     if constexpr (F32) {
+        float xf[NT], yf[NT], zf[NT];
+        int sr[NT];
+        float fx[NT], fy[NT], fz[NT], fi[NT];  // FP32 regular pairs (times 4 pi)
+#pragma unroll
+        for (int s = 0; s < NT; ++s) {
+            sr[s] = R.sr[tk[s]];
+            xf[s] = __double2float_rn(R.x[tk[s]][0]);
+            yf[s] = __double2float_rn(R.x[tk[s]][1]);
+            zf[s] = __double2float_rn(R.x[tk[s]][2]);
+            fx[s] = fy[s] = fz[s] = fi[s] = 0.f;
+        }
         extern __shared__ __align__(16) unsigned char tcore_dyn[];
         Stage32<Q>& S = *reinterpret_cast<Stage32<Q>*>(tcore_dyn);
         constexpr int TC = Stage32<Q>::TC;
-        int ncnt[NT];  // entries in this warp's list of each target (warp-uniform)
+        int ncnt[NT];  // entries in this warp's list of each slot (warp-uniform)
 #pragma unroll
         for (int s = 0; s < NT; ++s) ncnt[s] = 0;
-        // evaluate the listed near pairs of slot s: lane i takes entry i
+        // evaluate the listed near pairs of slot s (lane i takes entry i), sum over the
+        // warp in butterfly order, lane 0 adds the batch to R.N
         auto flush = [&](int s) {
-            if (lane < ncnt[s]) {
-                const int32_t j = R.near[warp][s][lane];
-                const int rj = A.region[j];
-                near_pair(s, j, A.u[j], A.electrode[rj] != 0 && rj != sr[s]);
-            }
+            double d[4] = {0.0, 0.0, 0.0, 0.0};
+            if (lane < ncnt[s]) near_pair(s, R.near[warp][s][lane], d);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) d[c] = wsum(d[c]);
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) R.N[tk[s]][warp][c] += d[c];
             __syncwarp();
             ncnt[s] = 0;
         };
+        constexpr int NS = Stage32<Q>::NS;
         const int64_t nch = (A.np + TC - 1) / TC;
         const int t = threadIdx.x;
-        stage_chunk<Q>(A, S, 0, 0, (int)min((int64_t)TC, A.np));
-        cp_async_commit();
+        // prologue: chunks 0 .. NS-2 in flight (one commit group per chunk, empty past the end)
+#pragma unroll
+        for (int p = 0; p < NS - 1; ++p) {
+            if (p < nch) stage_chunk<Q>(A, S, p, (int64_t)p * TC, (int)min((int64_t)TC, A.np - (int64_t)p * TC));
+            cp_async_commit();
+        }
         for (int64_t c = 0; c < nch; ++c) {
-            const int b = (int)(c & 1);
-            if (c + 1 < nch) {
-                const int64_t c1 = (c + 1) * TC;
-                stage_chunk<Q>(A, S, b ^ 1, c1, (int)min((int64_t)TC, A.np - c1));
-                cp_async_commit();
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
+            const int b = (int)(c % NS);
+            const int64_t cn = c + NS - 1;  // the chunk whose copies start now
+            if (cn < nch) stage_chunk<Q>(A, S, (int)(cn % NS), cn * TC, (int)min((int64_t)TC, A.np - cn * TC));
+            cp_async_commit();
+            cp_async_wait<NS - 1>();  // all but the NS-1 newest groups done: chunk c has landed
             cta_bar();
             const int64_t j = c * TC + t;
             const bool valid = t < TC && j < A.np;
@@ -237,10 +255,11 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask)
 #pragma unroll
                 for (int s = 0; s < NT; ++s) {
                     const bool far = is_far32(xf[s], yf[s], zf[s], h);
-                    nearf[s] = !far;
+                    nearf[s] = !far && s < nt;
                     const float m = far ? uf : 0.f;
                     fx[s] = fmaf(m, gx[s], fx[s]); fy[s] = fmaf(m, gy[s], fy[s]); fz[s] = fmaf(m, gz[s], fz[s]);
-                    if (far && elec && rj != sr[s]) fi[s] += gx[s] * nv.x + gy[s] * nv.y + gz[s] * nv.z;
+                    if (far && elec && rj != sr[s])
+                        fi[s] = fmaf(gz[s], nv.z, fmaf(gy[s], nv.y, fmaf(gx[s], nv.x, fi[s])));
                 }
             } else {
 #pragma unroll
@@ -259,61 +278,72 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask)
             }
             cta_bar();  // buffer b is refilled in the next iteration
         }
+        cp_async_wait<0>();  // no copies left in flight (the trailing groups are empty)
 #pragma unroll
         for (int s = 0; s < NT; ++s)
             if (ncnt[s] > 0) flush(s);
-    } else {
-        for (int64_t j = threadIdx.x; j < A.np; j += kLT) {
-            const int rj = A.region[j];
-            const bool elec = A.electrode[rj] != 0;
-            const double uj = A.u[j];
-            const double4 h = A.hdr64[j];
-            const double* gp = A.geo + GEO_STRIDE * j;
+        // per-slot warp sums of the regular pairs (fixed butterfly order)
 #pragma unroll
-            for (int s = 0; s < NT; ++s) {
-                const double* xs = R.x[tk[s]];
-                const bool mark = elec && rj != sr[s];
-                if (is_far64(xs[0], xs[1], xs[2], h)) {
+        for (int s = 0; s < NT; ++s) {
+            if (s >= nt) continue;
+            const float a = wsumf(fx[s]), bb = wsumf(fy[s]), cc = wsumf(fz[s]), dd = wsumf(fi[s]);
+            if (lane == 0) {
+                const int k = tk[s];
+                R.F[k][warp][0] = a; R.F[k][warp][1] = bb; R.F[k][warp][2] = cc; R.F[k][warp][3] = dd;
+                R.G[k][warp][0] = R.G[k][warp][1] = R.G[k][warp][2] = R.G[k][warp][3] = 0.0;
+            }
+        }
+    } else {
+        for (int s = 0; s < nt; ++s) {
+            const int k = (int)__fns(amask, 0, s + 1);
+            const double* xs = R.x[k];
+            const int srk = R.sr[k];
+            double q[4] = {0.0, 0.0, 0.0, 0.0}, d[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int64_t j = threadIdx.x; j < A.np; j += kLT) {
+                if (is_far64(xs[0], xs[1], xs[2], A.hdr64[j])) {
+                    const int rj = A.region[j];
+                    const double* gp = A.geo + GEO_STRIDE * j;
+                    const double uj = A.u[j];
                     double gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        const double4 nd = A.node64[j * Q + q];
+                    for (int qq = 0; qq < Q; ++qq) {
+                        const double4 nd = A.node64[j * Q + qq];
                         const double dx = xs[0] - nd.x, dy = xs[1] - nd.y, dz = xs[2] - nd.z;
                         const double ri = rsqrt(fma(dx, dx, fma(dy, dy, fma(dz, dz, 1e-200))));
                         const double t3 = nd.w * ri * ri * ri;
                         gx = fma(t3, dx, gx); gy = fma(t3, dy, gy); gz = fma(t3, dz, gz);
                     }
-                    qx[s] = fma(uj, gx, qx[s]); qy[s] = fma(uj, gy, qy[s]); qz[s] = fma(uj, gz, qz[s]);
-                    if (mark) qi[s] += gx * gp[GEO_N] + gy * gp[GEO_N + 1] + gz * gp[GEO_N + 2];
+                    q[0] = fma(uj, gx, q[0]); q[1] = fma(uj, gy, q[1]); q[2] = fma(uj, gz, q[2]);
+                    if (A.electrode[rj] != 0 && rj != srk) q[3] += gx * gp[GEO_N] + gy * gp[GEO_N + 1] + gz * gp[GEO_N + 2];
                 } else {
-                    near_pair(s, j, uj, mark);
+                    // near pair in place (slot index of k is s)
+                    const double* gp = A.geo + GEO_STRIDE * j;
+                    const int rj = A.region[j];
+                    const double uj = A.u[j];
+                    double S, Gx, Gy, Gz;
+                    tri_closed_form(gp, xs[0], xs[1], xs[2], false, S, Gx, Gy, Gz);
+                    d[0] = fma(uj, Gx, d[0]); d[1] = fma(uj, Gy, d[1]); d[2] = fma(uj, Gz, d[2]);
+                    if (A.electrode[rj] != 0 && rj != srk) d[3] += Gx * gp[GEO_N] + Gy * gp[GEO_N + 1] + Gz * gp[GEO_N + 2];
                 }
             }
-        }
-    }
-    // per-target warp sums (fixed butterfly order), lane 0 stores them
 #pragma unroll
-    for (int s = 0; s < NT; ++s) {
-        const float a = wsumf(fx[s]), bb = wsumf(fy[s]), cc = wsumf(fz[s]), dd = wsumf(fi[s]);
-        double e0 = nx[s], e1 = ny[s], e2 = nz[s], e3 = ni[s];
-        if (__any_sync(0xffffffffu, e0 != 0.0 || e1 != 0.0 || e2 != 0.0 || e3 != 0.0)) {
-            e0 = wsum(e0); e1 = wsum(e1); e2 = wsum(e2); e3 = wsum(e3);
-        }
-        double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
-        if constexpr (!F32) {
-            g0 = wsum(qx[s]); g1 = wsum(qy[s]); g2 = wsum(qz[s]); g3 = wsum(qi[s]);
-        }
-        if (lane == 0) {
-            const int k = tk[s];
-            R.F[k][warp][0] = a; R.F[k][warp][1] = bb; R.F[k][warp][2] = cc; R.F[k][warp][3] = dd;
-            R.N[k][warp][0] = e0; R.N[k][warp][1] = e1; R.N[k][warp][2] = e2; R.N[k][warp][3] = e3;
-            R.G[k][warp][0] = g0; R.G[k][warp][1] = g1; R.G[k][warp][2] = g2; R.G[k][warp][3] = g3;
+            for (int c = 0; c < 4; ++c) {
+                q[c] = wsum(q[c]);
+                d[c] = wsum(d[c]);
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    R.F[k][warp][c] = 0.f;
+                    R.G[k][warp][c] = q[c];
+                    R.N[k][warp][c] = d[c];
+                }
         }
     }
 }
 
 // The field at every posted point (all threads call this after the round's entry
-// barrier): the variant for the number of posting warps.
+// barrier): the variant for the number of posting warps, rounded up to 1, 2, 4 or 8.
 template <bool F32, int Q>
 __device__ __noinline__ void eval_round(const TArgs& A, Round& R)
 {
@@ -321,12 +351,18 @@ __device__ __noinline__ void eval_round(const TArgs& A, Round& R)
 #pragma unroll
     for (int k = 0; k < kLW; ++k)
         if (R.act[k]) amask |= 1u << k;
-    switch (__popc(amask)) {
-        case 1: eval_targets<F32, Q, 1>(A, R, amask); break;
-        case 2: eval_targets<F32, Q, 2>(A, R, amask); break;
-        case 3: eval_targets<F32, Q, 3>(A, R, amask); break;
-        case 4: eval_targets<F32, Q, 4>(A, R, amask); break;
-        default: break;
+    const int nt = __popc(amask);
+    if (nt == 0) return;
+    if constexpr (!F32) {
+        eval_targets<F32, Q, 1>(A, R, amask, nt);  // the FP64 form loops over the slots
+    } else if (nt == 1) {
+        eval_targets<F32, Q, 1>(A, R, amask, nt);
+    } else if (nt == 2) {
+        eval_targets<F32, Q, 2>(A, R, amask, nt);
+    } else if (nt <= 4) {
+        eval_targets<F32, Q, 4>(A, R, amask, nt);
+    } else {
+        eval_targets<F32, Q, 8>(A, R, amask, nt);
     }
 }
 
@@ -363,15 +399,19 @@ __device__ V4 field(const TArgs& A, Round& R, const double* x, int seed_region)
 }
 
 // A round in which the calling warp posts nothing; false if no warp posted a point
-// (then every warp of the CTA returns false from the same round).
+// (then every warp of the CTA is in this round and returns false from it).  *exh
+// receives the CTA's "no lines left" flag as it stands during the round: warps
+// change that flag only outside rounds, so in a round without posted points every
+// warp reads the same value.
 template <bool F32, int Q>
-__device__ bool idle_round(const TArgs& A, Round& R)
+__device__ bool idle_round(const TArgs& A, Round& R, const int* flag, int& exh)
 {
     if ((threadIdx.x & 31) == 0) R.act[threadIdx.x >> 5] = 0;
     cta_bar();
     bool any = false;
 #pragma unroll
     for (int k = 0; k < kLW; ++k) any = any || R.act[k] != 0;
+    exh = *(const volatile int*)flag;
     if (any) eval_round<F32, Q>(A, R);
     cta_bar();
     return any;
@@ -421,10 +461,16 @@ __device__ double event_g(const TArgs& A, Round& R, int seed_region, double s0, 
     return E.w + 0.5;
 }
 
+// Illinois regula falsi for the root of an event function g on [0, b], g(0) = ga,
+// g(b) = gb.  The event is detected at the end of the step (gb on the far side, or
+// zero: a root at b); if ga is already on that side (or zero) the condition held
+// where the sub-step starts and there is no crossing inside: the event is at 0.
 template <bool F32, int Q>
 __device__ double illinois(const TArgs& A, Round& R, int seed_region, double s0, int side, const double* x,
                            double K, const V4* E0c, double b, double ga, double gb, int ev)
 {
+    if (gb == 0.0) return b;
+    if (ga == 0.0 || (ga > 0.0) == (gb > 0.0)) return 0.0;
     double a = 0.0, c = b;
     int last = 0;
     for (int it = 0; it < 100; ++it) {
@@ -554,15 +600,19 @@ __device__ void trace_line(const TArgs& A, Round& R, const double* xs, Rec& rec,
 
 // Persistent driver: the warps of a tracer CTA take lines of the CTA's current mesh
 // from that mesh's counter (next[i], lines 0..L(i)-1) and trace them with
-// line_fn(A, R, mesh, line); a warp without a line joins the rounds of the others.
-// When every warp has run out, the CTA moves to another mesh with lines left.  The
-// counters only grow, so the loops end once all counters have passed their L.
-// args(i) gives mesh i's TArgs, L(i) its line count.
+// line_fn(A, R, mesh, line).  A CTA holds at most ceil(total / CTAs) lines at a
+// time (1..kLW), so the lines spread over all SMs instead of piling onto the CTAs
+// that start first; a warp without a line joins the rounds of the others and tries
+// again after each round.  When the mesh's counter has passed L the CTA leaves it
+// in the first round in which no warp posts a point (all warps together), and moves
+// to another mesh with lines left.  The counters only grow, so the loops end.
+// s_int: three shared ints (current mesh, lines held, no-lines-left flag).
 template <bool F32, int Q, class ArgsFn, class CountFn, class LineFn>
-__device__ void run_lines(ArgsFn args, CountFn L, int ninst, unsigned long long* next, TArgs& sA, Round& R,
-                          int& s_inst, LineFn line_fn)
+__device__ void run_lines(ArgsFn args, CountFn L, int ninst, int64_t total, unsigned long long* next,
+                          TArgs& sA, Round& R, int* s_int, LineFn line_fn)
 {
     const int lane = threadIdx.x & 31;
+    const int cap = (int)min((int64_t)kLW, max((int64_t)1, (total + gridDim.x - 1) / (int64_t)gridDim.x));
     int start = (int)(blockIdx.x % (unsigned)ninst);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -574,29 +624,49 @@ __device__ void run_lines(ArgsFn args, CountFn L, int ninst, unsigned long long*
                     break;
                 }
             }
-            s_inst = pick;
+            s_int[0] = pick;
+            s_int[1] = 0;
+            s_int[2] = 0;
             if (pick >= 0) sA = args(pick);
         }
         cta_bar();
-        const int ci = s_inst;
+        const int ci = s_int[0];
         if (ci < 0) break;
         const unsigned long long Lc = (unsigned long long)L(ci);
         for (;;) {
+            int got = 0;
             unsigned long long l = 0;
-            if (lane == 0) l = atomicAdd(&next[ci], 1ull);
+            if (lane == 0 && *(volatile int*)&s_int[2] == 0) {
+                if (atomicAdd(&s_int[1], 1) < cap) {
+                    l = atomicAdd(&next[ci], 1ull);
+                    if (l < Lc) {
+                        got = 1;
+                    } else {
+                        atomicExch(&s_int[2], 1);
+                        atomicSub(&s_int[1], 1);
+                    }
+                } else {
+                    atomicSub(&s_int[1], 1);
+                }
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
             l = __shfl_sync(0xffffffffu, l, 0);
-            if (l >= Lc) break;
-            line_fn(sA, R, ci, (int64_t)l);
-        }
-        while (idle_round<F32, Q>(sA, R)) {
+            if (got) {
+                line_fn(sA, R, ci, (int64_t)l);
+                if (lane == 0) atomicSub(&s_int[1], 1);
+                continue;
+            }
+            int exh = 0;
+            if (!idle_round<F32, Q>(sA, R, &s_int[2], exh) && exh) break;
         }
         start = ci;
-        cta_bar();  // sA and s_inst are rewritten next
+        cta_bar();  // sA and s_int are rewritten next
     }
 }
 
-// persistent grid of a tracer kernel: one CTA per SM at least, up to the resident
-// limit, never more CTAs than lines
+// persistent grid of a tracer kernel: every resident CTA slot of the GPU, but never
+// more CTAs than lines (with the per-CTA cap of run_lines, few lines spread one per
+// CTA, many lines fill every warp)
 template <class Kernel>
 inline unsigned lines_grid(Kernel k, size_t smem, int num_sms, int64_t lines)
 {
@@ -605,9 +675,8 @@ inline unsigned lines_grid(Kernel k, size_t smem, int num_sms, int64_t lines)
         cudaGetLastError();
         per_sm = 1;
     }
-    const int64_t cap = (int64_t)num_sms * std::max(per_sm, 1);
-    const int64_t want = std::max<int64_t>((lines + kLW - 1) / kLW, num_sms);
-    return (unsigned)std::max<int64_t>(1, std::min(std::min(want, cap), lines));
+    const int64_t slots = (int64_t)num_sms * std::max(per_sm, 1);
+    return (unsigned)std::max<int64_t>(1, std::min(slots, lines));
 }
 
 }  // namespace tcore
