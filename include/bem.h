@@ -116,6 +116,8 @@ typedef struct {
     int64_t matvecs[3];         /* matrix-free products, solver-internal ones included */
     int64_t gmres_iters;        /* Arnoldi steps */
     int64_t far32_variant;      /* FP32 kernel variant in use (1, 2 or 4; not reset) */
+    int64_t phi_pairs[3];       /* of pairs, those of product tiles holding only conductor rows,
+                                   summed for phi alone (their row equation needs no E) */
 } bem_counters;
 
 typedef struct bem_ctx bem_ctx;

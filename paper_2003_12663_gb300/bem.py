@@ -64,7 +64,8 @@ class bem_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("far_launches", ctypes.c_int64 * 3),
                 ("pairs", ctypes.c_int64 * 3), ("near_pairs", ctypes.c_int64 * 3),
                 ("far_ms", ctypes.c_double * 3), ("matvecs", ctypes.c_int64 * 3),
-                ("gmres_iters", ctypes.c_int64), ("far32_variant", ctypes.c_int64)]
+                ("gmres_iters", ctypes.c_int64), ("far32_variant", ctypes.c_int64),
+                ("phi_pairs", ctypes.c_int64 * 3)]
 
     def as_dict(self):
         out = {}

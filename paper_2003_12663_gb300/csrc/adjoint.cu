@@ -1025,7 +1025,7 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     if (rc && rc != BEM_ERR_NOT_CONVERGED) return rc;
 
     // 4. -mu^T (dA/dX) u, V0 and eps gradients
-    rc = matvec_impl(c, precision, 1, A.u, c->wvec);  // fills c->field with phi, E_PV at the centroids
+    rc = matvec_impl(c, precision, 1, A.u, c->wvec, true);  // fills c->field with phi, E_PV at the centroids
     if (rc) return rc;
     const int nreg = (int)c->regions.size();
     std::vector<double> h_epf(std::max(c->nfloat, 1), 1.0), h_af(std::max(c->nfloat, 1), 0.0);

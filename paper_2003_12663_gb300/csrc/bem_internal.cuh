@@ -52,6 +52,7 @@ struct bem_ctx {
     float4* qnode = nullptr;      // [np][Q] FP32 nodes with sigma folded into w (per call)
     float4* chunk_sph = nullptr;  // [np/32 rounded up] bounding sphere of 32 triangles' near zones
     int far32_tp = 2;             // FP32 kernel variant: 1 scalar, 2 or 4 packed target pairs
+    int64_t phi_tile_targets = 0; // centroid targets in tiles of conductor rows only (packed variant)
     float4* nrm32 = nullptr;      // [np] (unit normal in FP32, region index as int bits): field lines
     float* u32 = nullptr;         // [np] density rounded to FP32 for the field-line integrator
     float4* tgt_lo32 = nullptr;   // [np] centroid - tgt32
@@ -229,15 +230,20 @@ struct FarTargets {
     const double4* t64;      // FP64 targets (x,y,z,-) or nullptr
     const double* tpts;      // or raw double [M][3]
     int64_t M;
+    const int32_t* phi_kind = nullptr;  // row kinds: tiles of conductor rows may skip E (matvec only)
 };
 int far_splits(const bem_ctx* ctx, int precision, int64_t M);
+// centroid targets whose packed-kernel tile holds conductor rows only (0 for the scalar variant)
+int64_t far_phi_tile_targets(const bem_ctx* ctx);
 int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, int nrhs,
                int64_t ustride, int splits, double* part);
 
 // field.cu
 int launch_points_near(bem_ctx* ctx, int precision, int64_t M, const double* pts, const double* u,
                        const double* part, int splits, double* phi, double* E);
-int matvec_impl(bem_ctx* ctx, int precision, int nrhs, const double* x, double* y);
+// need_E: also fill ctx->field with E at the conductor rows (otherwise their regular
+// pairs may be summed for phi alone, which is all their row equation uses)
+int matvec_impl(bem_ctx* ctx, int precision, int nrhs, const double* x, double* y, bool need_E = false);
 // adjoint.cu: y = A^T v (one right-hand side)
 int matvecT_impl(bem_ctx* ctx, int precision, const double* v, double* y);
 

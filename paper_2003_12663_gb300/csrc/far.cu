@@ -18,6 +18,8 @@
 // FP32 form: per triangle the Q node contributions are summed in FP32, folded
 // into a per-chunk FP32 partial with u_j (masked to 0 for near pairs), and the
 // chunk partials are added with Kahan compensation.
+#include <algorithm>
+
 #include "bem_internal.cuh"
 
 namespace {
@@ -25,7 +27,8 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kTR32 = 4;
 constexpr int kTR64 = 2;
-constexpr int kTRdf = 2;
+constexpr int kTRdf = 2;   // double-FP32, one right-hand side
+constexpr int kTRdfN = 2;  // double-FP32, several right-hand sides (registers)
 constexpr int kPC32 = 32;
 constexpr int kPC64 = 16;
 
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(kThreads)
 k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_t M,
          const float4* __restrict__ hdr, const float4* __restrict__ qnode,
          const float4* __restrict__ chunk_sph, int64_t np, int64_t per_split,
-         double* __restrict__ part)
+         double* __restrict__ part, const int32_t* __restrict__ phi_kind)
 {
     constexpr int PC = kPC32;
     constexpr int TR = 2 * TP;
@@ -228,6 +231,17 @@ k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_
         tr += (hi - lo) * (hi - lo);
     }
     tr = 0.5f * sqrtf(tr) * 1.0001f + 1e-6f;
+    // a tile of conductor rows only needs phi (their row equation is phi = V0)
+    bool mine = phi_kind != nullptr;
+    if (phi_kind)
+#pragma unroll
+        for (int q = 0; q < TP; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t t = base + (2 * q + h) * kThreads + tid;
+                if (t < M) mine = mine && phi_kind[t] == BEM_CONDUCTOR;
+            }
+    const bool phi_only = __syncthreads_and(mine) != 0;
 
     float2 acc[TP][4], cmp[TP][4];
 #pragma unroll
@@ -254,7 +268,24 @@ k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_
         for (int q = 0; q < TP; ++q)
 #pragma unroll
             for (int c = 0; c < 4; ++c) cp[q][c] = make_float2(0.f, 0.f);
-        if (fast) {
+        if (fast && phi_only) {
+            for (int p = 0; p < npc; ++p) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    const float4 a = s_n2[p * Q + k][0], b = s_n2[p * Q + k][1];
+                    const float2 mx = make_float2(a.x, a.y), my = make_float2(a.z, a.w);
+                    const float2 mz = make_float2(b.x, b.y), w2 = make_float2(b.z, b.w);
+#pragma unroll
+                    for (int q = 0; q < TP; ++q) {
+                        const float2 dx = __fadd2_rn(tx[q], mx), dy = __fadd2_rn(ty[q], my),
+                                     dz = __fadd2_rn(tz[q], mz);
+                        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+                        const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                        cp[q][0] = __fadd2_rn(cp[q][0], __fmul2_rn(w2, ri));
+                    }
+                }
+            }
+        } else if (fast) {
             for (int p = 0; p < npc; ++p) {
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
@@ -274,6 +305,32 @@ k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_
                         cp[q][2] = __ffma2_rn(t3, dy, cp[q][2]);
                         cp[q][3] = __ffma2_rn(t3, dz, cp[q][3]);
                     }
+                }
+            }
+        } else if (phi_only) {
+            for (int p = 0; p < npc; ++p) {
+                float2 ps[TP];
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    const float4 a = s_n2[p * Q + k][0], b = s_n2[p * Q + k][1];
+                    const float2 mx = make_float2(a.x, a.y), my = make_float2(a.z, a.w);
+                    const float2 mz = make_float2(b.x, b.y), w2 = make_float2(b.z, b.w);
+#pragma unroll
+                    for (int q = 0; q < TP; ++q) {
+                        const float2 dx = __fadd2_rn(tx[q], mx), dy = __fadd2_rn(ty[q], my),
+                                     dz = __fadd2_rn(tz[q], mz);
+                        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+                        const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                        const float2 t = __fmul2_rn(w2, ri);
+                        ps[q] = k == 0 ? t : __fadd2_rn(ps[q], t);
+                    }
+                }
+                const float4 h = s_hdr[p];
+#pragma unroll
+                for (int q = 0; q < TP; ++q) {
+                    const bool f0 = is_far32(tx[q].x, ty[q].x, tz[q].x, h);
+                    const bool f1 = is_far32(tx[q].y, ty[q].y, tz[q].y, h);
+                    cp[q][0] = __fadd2_rn(cp[q][0], make_float2(f0 ? ps[q].x : 0.f, f1 ? ps[q].y : 0.f));
                 }
             }
         } else {
@@ -433,12 +490,52 @@ k_far64(const double4* __restrict__ t64, const double* __restrict__ tpts, int64_
 // A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2).  The
 // operations are the error-free transformations of Knuth (two-sum) and Dekker
 // (two-product, here with an FMA), written with explicit-rounding intrinsics so
-// that the compiler cannot fuse or reorder them.  They run on pairs of values: the
-// f32x2 instructions round each lane on its own (IEEE round-to-nearest), so a lane
-// computes exactly the scalar double-FP32 arithmetic of its value.
+// that the compiler cannot fuse or reorder them.
 struct df32 {
     float hi, lo;
 };
+
+__device__ __forceinline__ df32 quick_two_sum(float a, float b)  // needs |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df32 df_add(df32 a, df32 b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return quick_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df32 df_neg(df32 a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ df32 df_sqr(df32 a)
+{
+    const float p = __fmul_rn(a.hi, a.hi);
+    const float e = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, __fmaf_rn(a.hi, a.hi, -p));
+    return quick_two_sum(p, e);
+}
+
+// 1/sqrt(x): the FP32 estimate y, then one Newton step y + y (1 - x y^2) / 2 in
+// double-FP32 (the error goes from ~2^-22 to ~2^-44).
+__device__ __forceinline__ df32 df_rsqrt(df32 x)
+{
+    const float y = rsqrtf(x.hi);
+    const df32 yy = {__fmul_rn(y, y), __fmaf_rn(y, y, -__fmul_rn(y, y))};
+    const df32 t = df_mul(x, yy);
+    const float d = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+    return quick_two_sum(y, __fmul_rn(__fmul_rn(y, d), 0.5f));
+}
 
 __device__ __forceinline__ df32 df_from(double v)
 {
@@ -446,64 +543,13 @@ __device__ __forceinline__ df32 df_from(double v)
     return {h, __double2float_rn(v - (double)h)};
 }
 
-struct df2 {
-    float2 hi, lo;
-};
-
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
-
-// two-sum of a + b with |a| >= |b|
-__device__ __forceinline__ df2 quick_two_sum2(float2 a, float2 b)
-{
-    const float2 s = __fadd2_rn(a, b);
-    return {s, sub2(b, sub2(s, a))};
-}
-
-__device__ __forceinline__ df2 df2_add(df2 a, df2 b)
-{
-    const float2 s = __fadd2_rn(a.hi, b.hi);
-    const float2 bb = sub2(s, a.hi);
-    const float2 e = __fadd2_rn(sub2(a.hi, sub2(s, bb)), sub2(b.hi, bb));
-    return quick_two_sum2(s, __fadd2_rn(e, __fadd2_rn(a.lo, b.lo)));
-}
-
-__device__ __forceinline__ df2 df2_mul(df2 a, df2 b)
-{
-    const float2 p = __fmul2_rn(a.hi, b.hi);
-    float2 e = __ffma2_rn(a.hi, b.hi, neg2(p));
-    e = __ffma2_rn(a.hi, b.lo, __ffma2_rn(a.lo, b.hi, e));
-    return quick_two_sum2(p, e);
-}
-
-__device__ __forceinline__ df2 df2_sqr(df2 a)
-{
-    const float2 p = __fmul2_rn(a.hi, a.hi);
-    const float2 e = __ffma2_rn(__fadd2_rn(a.hi, a.hi), a.lo, __ffma2_rn(a.hi, a.hi, neg2(p)));
-    return quick_two_sum2(p, e);
-}
-
-// 1/sqrt(x): the FP32 estimate y, then one Newton step y + y (1 - x y^2) / 2 in
-// double-FP32 (the error goes from ~2^-22 to ~2^-44).
-__device__ __forceinline__ df2 df2_rsqrt(df2 x)
-{
-    const float2 y = make_float2(rsqrtf(x.hi.x), rsqrtf(x.hi.y));
-    const float2 y2 = __fmul2_rn(y, y);
-    const df2 yy = {y2, __ffma2_rn(y, y, neg2(y2))};
-    const df2 t = df2_mul(x, yy);
-    const float2 d = sub2(sub2(f2(1.0f), t.hi), t.lo);
-    return quick_two_sum2(y, __fmul2_rn(__fmul2_rn(y, d), f2(0.5f)));
-}
-
 // Regular pairs in double-FP32, centroid targets only (the refinement residual).
 // Near pairs are masked with the FP32 classification, exactly as in k_far32; the
 // consumer adds per near pair the value that turns the result into the FP64
-// classification's (see k_near_values).  Every thread holds two targets (base + tid
-// and base + kThreads + tid) as the two lanes of f32x2 values.  NR right-hand sides
-// (densities u + r * ustride) share one pass over the nodes: the node sums of a pair
-// do not depend on the density; each right-hand side's arithmetic is that of NR = 1.
-template <int Q, int NR>
+// classification's (see k_near_values).  NR right-hand sides (densities
+// u + r * ustride) share one pass over the nodes: the node sums of a pair do not
+// depend on the density; each right-hand side's arithmetic is that of NR = 1.
+template <int TR, int Q, int NR>
 __global__ void __launch_bounds__(kThreads)
 k_far_df(const float4* __restrict__ t32, const float4* __restrict__ t32lo, int64_t M,
          const float4* __restrict__ hdr, const float4* __restrict__ node,
@@ -516,27 +562,27 @@ k_far_df(const float4* __restrict__ t32, const float4* __restrict__ t32lo, int64
     __shared__ float4 s_node[PC * Q];
     __shared__ float4 s_nlo[PC * Q];
     const int tid = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * (kThreads * kTRdf);
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * TR);
     const int split = blockIdx.y;
     const int64_t p0 = (int64_t)split * per_split;
     const int64_t p1 = min(np, p0 + per_split);
 
-    df2 tx, ty, tz;
-    float fx[2], fy[2], fz[2];  // FP32 targets of the classification
-    {
-        const int64_t ta = min(base + tid, M - 1), tb = min(base + kThreads + tid, M - 1);
-        const float4 ha = t32[ta], la = t32lo[ta], hb = t32[tb], lb = t32lo[tb];
-        tx = {make_float2(ha.x, hb.x), make_float2(la.x, lb.x)};
-        ty = {make_float2(ha.y, hb.y), make_float2(la.y, lb.y)};
-        tz = {make_float2(ha.z, hb.z), make_float2(la.z, lb.z)};
-        fx[0] = ha.x; fy[0] = ha.y; fz[0] = ha.z;
-        fx[1] = hb.x; fy[1] = hb.y; fz[1] = hb.z;
+    df32 tx[TR], ty[TR], tz[TR];
+    float fx[TR], fy[TR], fz[TR];  // FP32 targets of the classification
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int64_t t = min(base + r * kThreads + tid, M - 1);
+        const float4 h = t32[t], l = t32lo[t];
+        tx[r] = {h.x, l.x}; ty[r] = {h.y, l.y}; tz[r] = {h.z, l.z};
+        fx[r] = h.x; fy[r] = h.y; fz[r] = h.z;
     }
-    df2 acc[NR][4];
+    df32 acc[NR][TR][4];
 #pragma unroll
     for (int q = 0; q < NR; ++q)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[q][c] = {f2(0.f), f2(0.f)};
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[q][r][c] = {0.f, 0.f};
 
     for (int64_t c0 = p0; c0 < p1; c0 += PC) {
         const int npc = (int)min((int64_t)PC, p1 - c0);
@@ -555,55 +601,57 @@ k_far_df(const float4* __restrict__ t32, const float4* __restrict__ t32lo, int64
         }
         __syncthreads();
         for (int p = 0; p < npc; ++p) {
-            df2 ps, gx, gy, gz;
+            df32 ps[TR], gx[TR], gy[TR], gz[TR];
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
                 const float4 nh = s_node[p * Q + k], nl = s_nlo[p * Q + k];
-                const df2 w = {f2(nh.w), f2(nl.w)};
-                const df2 dx = df2_add(tx, {f2(-nh.x), f2(-nl.x)});
-                const df2 dy = df2_add(ty, {f2(-nh.y), f2(-nl.y)});
-                const df2 dz = df2_add(tz, {f2(-nh.z), f2(-nl.z)});
-                df2 r2 = df2_add(df2_add(df2_sqr(dx), df2_sqr(dy)), df2_sqr(dz));
-                r2.hi = make_float2(fmaxf(r2.hi.x, 1e-20f), fmaxf(r2.hi.y, 1e-20f));
-                const df2 ri = df2_rsqrt(r2);
-                const df2 t = df2_mul(w, ri);
-                const df2 t3 = df2_mul(t, df2_sqr(ri));
-                if (k == 0) {
-                    ps = t;
-                    gx = df2_mul(t3, dx); gy = df2_mul(t3, dy); gz = df2_mul(t3, dz);
-                } else {
-                    ps = df2_add(ps, t);
-                    gx = df2_add(gx, df2_mul(t3, dx));
-                    gy = df2_add(gy, df2_mul(t3, dy));
-                    gz = df2_add(gz, df2_mul(t3, dz));
+                const df32 w = {nh.w, nl.w};
+#pragma unroll
+                for (int r = 0; r < TR; ++r) {
+                    const df32 dx = df_add(tx[r], df_neg({nh.x, nl.x}));
+                    const df32 dy = df_add(ty[r], df_neg({nh.y, nl.y}));
+                    const df32 dz = df_add(tz[r], df_neg({nh.z, nl.z}));
+                    df32 r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+                    r2.hi = fmaxf(r2.hi, 1e-20f);
+                    const df32 ri = df_rsqrt(r2);
+                    const df32 t = df_mul(w, ri);
+                    const df32 t3 = df_mul(t, df_sqr(ri));
+                    if (k == 0) {
+                        ps[r] = t;
+                        gx[r] = df_mul(t3, dx); gy[r] = df_mul(t3, dy); gz[r] = df_mul(t3, dz);
+                    } else {
+                        ps[r] = df_add(ps[r], t);
+                        gx[r] = df_add(gx[r], df_mul(t3, dx));
+                        gy[r] = df_add(gy[r], df_mul(t3, dy));
+                        gz[r] = df_add(gz[r], df_mul(t3, dz));
+                    }
                 }
             }
             const float4 h = s_hdr[p];
-            const bool far0 = is_far32(fx[0], fy[0], fz[0], h), far1 = is_far32(fx[1], fy[1], fz[1], h);
 #pragma unroll
-            for (int q = 0; q < NR; ++q) {
-                const float2 up = s_u[q][p];
-                const df2 m = {make_float2(far0 ? up.x : 0.f, far1 ? up.x : 0.f),
-                               make_float2(far0 ? up.y : 0.f, far1 ? up.y : 0.f)};
-                acc[q][0] = df2_add(acc[q][0], df2_mul(m, ps));
-                acc[q][1] = df2_add(acc[q][1], df2_mul(m, gx));
-                acc[q][2] = df2_add(acc[q][2], df2_mul(m, gy));
-                acc[q][3] = df2_add(acc[q][3], df2_mul(m, gz));
+            for (int r = 0; r < TR; ++r) {
+                const bool far = is_far32(fx[r], fy[r], fz[r], h);
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    const float2 up = s_u[q][p];
+                    const df32 m = far ? df32{up.x, up.y} : df32{0.f, 0.f};
+                    acc[q][r][0] = df_add(acc[q][r][0], df_mul(m, ps[r]));
+                    acc[q][r][1] = df_add(acc[q][r][1], df_mul(m, gx[r]));
+                    acc[q][r][2] = df_add(acc[q][r][2], df_mul(m, gy[r]));
+                    acc[q][r][3] = df_add(acc[q][r][3], df_mul(m, gz[r]));
+                }
             }
         }
     }
 #pragma unroll
     for (int q = 0; q < NR; ++q)
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < TR; ++r) {
             const int64_t t = base + r * kThreads + tid;
             if (t < M) {
                 double* o = part + (((int64_t)q * gridDim.y + split) * M + t) * 4;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float hi = r ? acc[q][c].hi.y : acc[q][c].hi.x, lo = r ? acc[q][c].lo.y : acc[q][c].lo.x;
-                    o[c] = (double)hi + (double)lo;
-                }
+                for (int c = 0; c < 4; ++c) o[c] = (double)acc[q][r][c].hi + (double)acc[q][r][c].lo;
             }
         }
 }
@@ -622,13 +670,13 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
         BEM_LAUNCH_CHECK(ctx);
         const int tr = 2 * ctx->far32_tp;
         dim3 grid((unsigned)((T.M + kThreads * tr - 1) / (kThreads * tr)), (unsigned)splits);
-#define FAR32P(TP)                                                                                \
-    if (raw)                                                                                      \
-        k_far32p<TP, Q, true><<<grid, kThreads, 0, ctx->stream>>>(                                \
-            nullptr, T.tpts, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part);   \
-    else                                                                                          \
-        k_far32p<TP, Q, false><<<grid, kThreads, 0, ctx->stream>>>(                               \
-            T.t32, nullptr, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part)
+#define FAR32P(TP)                                                                                     \
+    if (raw)                                                                                           \
+        k_far32p<TP, Q, true><<<grid, kThreads, 0, ctx->stream>>>(                                     \
+            nullptr, T.tpts, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part, nullptr); \
+    else                                                                                               \
+        k_far32p<TP, Q, false><<<grid, kThreads, 0, ctx->stream>>>(                                    \
+            T.t32, nullptr, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part, T.phi_kind)
         if (ctx->far32_tp == 4) {
             FAR32P(4);
         } else {
@@ -638,7 +686,7 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
     } else if (precision == kPrecDF) {
         if (raw || !T.t32lo) return set_err(ctx, BEM_ERR_ARG, "double-FP32 pass needs centroid targets");
         dim3 grid((unsigned)((T.M + kThreads * kTRdf - 1) / (kThreads * kTRdf)), (unsigned)splits);
-        k_far_df<Q, 1><<<grid, kThreads, 0, ctx->stream>>>(
+        k_far_df<kTRdf, Q, 1><<<grid, kThreads, 0, ctx->stream>>>(
             T.t32, T.t32lo, T.M, ctx->hdr32, ctx->node32, ctx->node_lo32, u, 0, np, per_split, part);
     } else if (precision == BEM_MIXED) {
         dim3 grid((unsigned)((T.M + kThreads * kTR32 - 1) / (kThreads * kTR32)), (unsigned)splits);
@@ -669,9 +717,9 @@ int launch_df_multi(bem_ctx* ctx, const FarTargets& T, const double* u, int nrhs
     if (T.tpts || !T.t32lo) return set_err(ctx, BEM_ERR_ARG, "double-FP32 pass needs centroid targets");
     const int64_t np = ctx->np;
     const int64_t per_split = ((np + splits - 1) / splits + kPC32 - 1) / kPC32 * kPC32;
-    dim3 grid((unsigned)((T.M + kThreads * kTRdf - 1) / (kThreads * kTRdf)), (unsigned)splits);
+    dim3 grid((unsigned)((T.M + kThreads * kTRdfN - 1) / (kThreads * kTRdfN)), (unsigned)splits);
 #define DFM(NR)                                                                                       \
-    k_far_df<Q, NR><<<grid, kThreads, 0, ctx->stream>>>(T.t32, T.t32lo, T.M, ctx->hdr32,         \
+    k_far_df<kTRdfN, Q, NR><<<grid, kThreads, 0, ctx->stream>>>(T.t32, T.t32lo, T.M, ctx->hdr32,         \
                                                                ctx->node32, ctx->node_lo32, u, ustride, \
                                                                np, per_split, part)
     switch (nrhs) {
@@ -702,6 +750,21 @@ int far_splits(const bem_ctx* ctx, int precision, int64_t M)
     return (int)s;
 }
 
+int64_t far_phi_tile_targets(const bem_ctx* ctx)
+{
+    if (ctx->far32_tp <= 1) return 0;
+    const int64_t tile = (int64_t)kThreads * 2 * ctx->far32_tp, np = ctx->np;
+    int64_t n = 0;
+    for (int64_t t0 = 0; t0 < np; t0 += tile) {
+        const int64_t t1 = std::min(np, t0 + tile);
+        bool all = true;
+        for (int64_t t = t0; t < t1 && all; ++t)
+            all = ctx->regions[ctx->h_region[t]].kind == BEM_CONDUCTOR;
+        if (all) n += t1 - t0;
+    }
+    return n;
+}
+
 int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, int nrhs,
                int64_t ustride, int splits, double* part)
 {
@@ -729,6 +792,8 @@ int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u
         ctx->cnt.far_launches[pi] += 1;
         ctx->cnt.pairs[pi] += T.M * ctx->np;
         if (T.tpts == nullptr) ctx->cnt.near_pairs[pi] += ctx->nnz_prec[pi];  // centroid targets
+        if (precision == BEM_MIXED && T.phi_kind && T.tpts == nullptr)
+            ctx->cnt.phi_pairs[pi] += ctx->phi_tile_targets * ctx->np;
         timing_begin(ctx, pi);
         switch (ctx->g) {
             case 1: rc = launch_q<1>(ctx, precision, T, ur, splits, pr); break;

@@ -380,13 +380,13 @@ int assemble_dispatch(bem_ctx* c, int64_t row0, int64_t row1, double* A, int64_t
 
 }  // namespace
 
-int matvec_impl(bem_ctx* c, int precision, int nrhs, const double* x, double* y)
+int matvec_impl(bem_ctx* c, int precision, int nrhs, const double* x, double* y, bool need_E)
 {
     const int64_t np = c->np, n = c->nunk;
     const int splits = far_splits(c, precision, np);
     if ((size_t)splits * np * 4 * nrhs > c->part_cap)
         return set_err(c, BEM_ERR_CAPACITY, "far workspace too small");
-    FarTargets T{c->tgt32, c->tgt_lo32, c->tgt64, nullptr, np};
+    FarTargets T{c->tgt32, c->tgt_lo32, c->tgt64, nullptr, np, need_E ? nullptr : c->row_kind};
     int rc = launch_far(c, precision, T, x, nrhs, n, splits, c->part);
     if (rc) return rc;
     c->cnt.matvecs[precision] += nrhs;

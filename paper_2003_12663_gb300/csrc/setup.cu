@@ -548,6 +548,7 @@ static int tune_far32(bem_ctx* c)
         c->far32_tp = 2;
     }
     timing_drain(c);
+    c->phi_tile_targets = far_phi_tile_targets(c);
     c->cnt = bem_counters{};
     c->cnt.far32_variant = c->far32_tp;
     BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 2 * sizeof(unsigned long long), c->stream));
