@@ -224,11 +224,11 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
         }
         for (int64_t c = 0; c < nch; ++c) {
             const int b = (int)(c % NS);
-            const int64_t cn = c + NS - 1;  // the chunk whose copies start now
+            cp_async_wait<NS - 2>();  // chunks 0..c have landed (NS-2 newer groups may be in flight)
+            cta_bar();                // ... for every thread; and every thread is done with chunk c-1
+            const int64_t cn = c + NS - 1;  // its buffer, (c-1) % NS, takes chunk c+NS-1 now
             if (cn < nch) stage_chunk<Q>(A, S, (int)(cn % NS), cn * TC, (int)min((int64_t)TC, A.np - cn * TC));
             cp_async_commit();
-            cp_async_wait<NS - 1>();  // all but the NS-1 newest groups done: chunk c has landed
-            cta_bar();
             const int64_t j = c * TC + t;
             const bool valid = t < TC && j < A.np;
             bool nearf[NT];
@@ -276,7 +276,6 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
                 __syncwarp();
                 ncnt[s] += cnt;
             }
-            cta_bar();  // buffer b is refilled in the next iteration
         }
         cp_async_wait<0>();  // no copies left in flight (the trailing groups are empty)
 #pragma unroll
