@@ -103,9 +103,12 @@ k_adj_forward(TArgs A, const double* __restrict__ seeds, int64_t L, unsigned lon
 }
 
 // ---------------------------------------------------------------- CTA passes
+// CTA sums of NV values in a fixed order, returned to every thread: warp butterflies,
+// then lane i adds value i over the warps (in warp order) and shuffles it to all lanes
 template <int NV>
 __device__ void block_sum_n(double* v, double* sh)
 {
+    static_assert(NV <= 32, "one lane per value");
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = wsum(v[i]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -114,13 +117,12 @@ __device__ void block_sum_n(double* v, double* sh)
 #pragma unroll
         for (int i = 0; i < NV; ++i) sh[i * kWarps + warp] = v[i];
     __syncthreads();
+    const int li = min(lane, NV - 1);
+    double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        double s = 0.0;
+    for (int w = 0; w < kWarps; ++w) s += sh[li * kWarps + w];
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += sh[i * kWarps + w];
-        v[i] = s;
-    }
+    for (int i = 0; i < NV; ++i) v[i] = __shfl_sync(0xffffffffu, s, i);
 }
 
 // E(x) and its Jacobian J = dE/dx (symmetric: xx, yy, zz, xy, xz, yz) -> out[9]

@@ -73,15 +73,18 @@ __global__ void k_rows(int64_t np, int splits, const double* __restrict__ part,
 }
 
 // One block per floating body: y[N+f] = sum of its rows' neutrality terms, in a
-// fixed order (deterministic).
+// fixed order (deterministic).  A body has thousands of rows: 1024 threads keep the
+// gathers in flight.
+constexpr int kNeutThreads = 1024;
 __global__ void k_neutrality(int64_t np, const int32_t* __restrict__ rows,
                              const int32_t* __restrict__ off, const double* __restrict__ neut,
                              double* __restrict__ y)
 {
-    __shared__ double sh[256];
+    __shared__ double sh[kNeutThreads];
     const int f = blockIdx.x;
     double s = 0.0;
-    for (int k = off[f] + threadIdx.x; k < off[f + 1]; k += blockDim.x) s += neut[rows[k]];
+#pragma unroll 4
+    for (int k = off[f] + threadIdx.x; k < off[f + 1]; k += kNeutThreads) s += neut[rows[k]];
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -402,7 +405,7 @@ int matvec_impl(bem_ctx* c, int precision, int nrhs, const double* x, double* y,
             c->neut + r * np, c->field + (size_t)r * np * 4);
         BEM_LAUNCH_CHECK(c);
         if (c->nfloat > 0) {
-            k_neutrality<<<c->nfloat, 256, 0, c->stream>>>(np, c->float_rows, c->float_off,
+            k_neutrality<<<c->nfloat, kNeutThreads, 0, c->stream>>>(np, c->float_rows, c->float_off,
                                                             c->neut + r * np, y + r * n);
             BEM_LAUNCH_CHECK(c);
         }

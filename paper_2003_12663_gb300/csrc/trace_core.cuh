@@ -365,18 +365,25 @@ __device__ __noinline__ void eval_round(const TArgs& A, Round& R)
     }
 }
 
-// the field at warp w's point from the round's partial sums (fixed order)
+// the field at warp w's point from the round's partial sums: lane 4a+c (a = 0 FP32
+// regular pairs, 1 closed-form pairs, 2 FP64 regular pairs; c = component) adds its
+// sum over the warps in order, and the twelve sums reach every lane by shuffles
+// (one FP64 add per warp and lane instead of twelve)
 __device__ __forceinline__ V4 round_result(const Round& R, int w)
 {
-    double f[4] = {0.0, 0.0, 0.0, 0.0}, n[4] = {0.0, 0.0, 0.0, 0.0}, g[4] = {0.0, 0.0, 0.0, 0.0};
+    const int lane = threadIdx.x & 31;
+    const int a = min(lane >> 2, 2), c = lane & 3;
+    double v = 0.0;
 #pragma unroll
-    for (int v = 0; v < kLW; ++v)
+    for (int u = 0; u < kLW; ++u)
+        v += a == 0 ? (double)R.F[w][u][c] : (a == 1 ? R.N[w][u][c] : R.G[w][u][c]);
+    double f[4], n[4], g[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            f[c] += (double)R.F[w][v][c];
-            n[c] += R.N[w][v][c];
-            g[c] += R.G[w][v][c];
-        }
+    for (int k = 0; k < 4; ++k) {
+        f[k] = __shfl_sync(0xffffffffu, v, k);
+        n[k] = __shfl_sync(0xffffffffu, v, 4 + k);
+        g[k] = __shfl_sync(0xffffffffu, v, 8 + k);
+    }
     return V4{n[0] + kInv4Pi * (g[0] + f[0]), n[1] + kInv4Pi * (g[1] + f[1]),
               n[2] + kInv4Pi * (g[2] + f[2]), n[3] + kInv4Pi * (g[3] + f[3])};
 }
