@@ -11,7 +11,8 @@ What it computes (paper sections / equations):
   Duffy-transformed Gauss rule (C part, ``bem_oracle.c``);
 * the classification of Sec. 4: a pair is regular iff D > eta*R, with D the
   distance of the target to the triangle's circumcentre and R the circumradius;
-* the collocation system of Eqs. (Final1)-(Final4), discretised by
+* the collocation system of Eqs. (Final1)-(Final4), with thin floating sheets
+  by Eq. (sheets), discretised by
   piecewise-constant sigma on flat triangles with centroid collocation (Sec. 3);
 * its solution by a dense LU factorisation (LAPACK through numpy);
 * phi and E at arbitrary points (field formula at the end of Sec. 2);
@@ -97,6 +98,7 @@ def _trace_call(L, seeds, analytic, q, P, u, tp):
     else:
         uu = _c(u[: P.N], np.float64)
         reg = _c(P.mesh.region, np.int32)
+        # bodies whose surface ends a field line; a thin sheet has no inside
         elec = np.array([1 if r["kind"] in ("conductor", "floating") else 0 for r in P.mesh.regions],
                         np.int32)
         ru, rwu, rv, rwv = P.rule
@@ -251,6 +253,10 @@ class Problem:
         Row N+f (charge neutrality of floating conductor f, Eq. Final4, centroid
         rule, divided by the conductor's area):
           sum_{i in f} A_i eps+ (u_i/2 + (K'u)_i) / area_f             = 0
+        A thin floating sheet (one surface, kind "sheet") has the potential rows
+        of a floating conductor; its neutrality row takes the fields of both
+        sides (Eq. sheets):
+          sum_{i in f} A_i ((eps+ + eps-)/2 u_i + (eps+ - eps-) (K'u)_i) / area_f = 0
         """
         N, F = self.N, self.F
         A = np.zeros((N + F, N + F))
@@ -274,6 +280,15 @@ class Problem:
                     row = Kp[ii].copy()
                     row[i] += 0.5
                     neut[f] += self.area[i] * R.get("eps_plus", 1.0) * row
+                    area_f[f] += self.area[i]
+                elif R["kind"] == "sheet":
+                    f = R["floating_id"]
+                    A[i, :N] = S[ii]
+                    A[i, N + f] = -1.0
+                    ep, em = R["eps_plus"], R["eps_minus"]
+                    row = (ep - em) * Kp[ii]
+                    row[i] += 0.5 * (ep + em)
+                    neut[f] += self.area[i] * row
                     area_f[f] += self.area[i]
                 elif R["kind"] == "dielectric":
                     ep, em = R["eps_plus"], R["eps_minus"]

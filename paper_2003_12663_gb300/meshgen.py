@@ -7,13 +7,17 @@ oracle are fed with, so that the two can be compared on identical inputs.
 Conventions (Sec. 2 of the paper, Fig. 2): every body is a closed surface made
 of flat triangles; each triangle's vertices are ordered counter-clockwise when
 seen from the side its normal points to, and that normal points out of the body
-(into the exterior medium, the "+" side).
+(into the exterior medium, the "+" side).  A thin floating sheet is a single,
+possibly open surface whose normal picks its "+" side (Eq. sheets).
 
 Region descriptors are plain dicts::
 
     {"kind": "conductor",  "V0": 1.0}
     {"kind": "floating",   "floating_id": 0, "eps_plus": 1.0}
     {"kind": "dielectric", "eps_plus": 1.0, "eps_minus": 4.0}
+    {"kind": "sheet",      "floating_id": 1, "eps_plus": 1.0, "eps_minus": 4.0}
+
+Floating conductors and sheets share one numbering of floating bodies.
 """
 from __future__ import annotations
 
@@ -22,7 +26,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-KIND_CODE = {"conductor": 0, "floating": 1, "dielectric": 2}
+KIND_CODE = {"conductor": 0, "floating": 1, "dielectric": 2, "sheet": 3}
+FLOATING_KINDS = ("floating", "sheet")
 
 
 @dataclass
@@ -45,7 +50,7 @@ class Mesh:
 
     @property
     def n_floating(self) -> int:
-        ids = {r["floating_id"] for r in self.regions if r["kind"] == "floating"}
+        ids = {r["floating_id"] for r in self.regions if r["kind"] in FLOATING_KINDS}
         return len(ids)
 
     @property
@@ -265,6 +270,28 @@ def closed_cylinder(radius: float, height: float, center, K: int, n_z: int):
     return X, tri.astype(np.int32)
 
 
+def open_cylinder(radius: float, z0: float, z1: float, n_t: int, n_z: int):
+    """Open cylindrical sheet (axis z, no caps, z0 <= z <= z1): a grid of n_t x n_z
+    cells, each split into two triangles, normals pointing away from the axis."""
+    z = z0 + (z1 - z0) * np.arange(n_z + 1) / n_z
+    th = 2.0 * np.pi * np.arange(n_t) / n_t
+    X = np.array([[radius * np.cos(t), radius * np.sin(t), zk] for zk in z for t in th])
+    side = lambda i, k: k * n_t + (i % n_t)
+    tris = []
+    for k in range(n_z):
+        for i in range(n_t):
+            p00, p10, p11, p01 = side(i, k), side(i + 1, k), side(i + 1, k + 1), side(i, k + 1)
+            tris += [(p00, p10, p11), (p00, p11, p01)]
+    tri = np.array(tris, dtype=np.int64)
+
+    def outward(p):
+        out = p.copy()
+        out[:, 2] = 0.0
+        return out
+
+    return X, _orient_outward(X, tri, outward).astype(np.int32)
+
+
 def jitter(X: np.ndarray, tri: np.ndarray, frac: float, seed: int, movable=None) -> np.ndarray:
     """Move each vertex by U(-frac, frac) * (mean length of its edges), per coordinate."""
     rng = np.random.default_rng(seed)
@@ -328,6 +355,53 @@ def device_mesh(scale: float = 1.0, seed: int = 2, jitter_frac: float = 0.005,
     info = {"body": "device", "scale": scale, "sphere_freq": m, "torus": (n_u, n_v),
             "cylinder": (K, n_z), "counts": (len(Ts), len(Tt), len(Tc)), "seed": seed,
             "jitter": jitter_frac}
+    return Mesh(X, tri, region, regions, info)
+
+
+def sphere_in_sheet_mesh(level: int, a: float = 1.0, b: float = 2.0, eps_in: float = 4.0,
+                         eps_out: float = 1.0, V0: float = 1.0) -> Mesh:
+    """Conductor sphere (radius a, potential V0) inside a closed thin floating sheet
+    (radius b), with permittivity eps_in between them and eps_out outside: the
+    concentric case of Eq. sheets, which has a closed-form solution."""
+    X1, T1 = icosphere(level, a)
+    X2, T2 = icosphere(level, b)
+    X, tri, region = _merge([(X1, T1, 0), (X2, T2, 1)])
+    regions = [{"kind": "conductor", "V0": V0},
+               {"kind": "sheet", "floating_id": 0, "eps_plus": eps_out, "eps_minus": eps_in}]
+    return Mesh(X, tri, region, regions, {"body": "sphere_in_sheet", "level": level, "a": a, "b": b,
+                                          "eps_in": eps_in, "eps_out": eps_out})
+
+
+BUSHING_FOIL_RADII = (0.25, 0.40, 0.55, 0.70, 0.85)
+BUSHING_FOIL_LENGTHS = (3.0, 2.6, 2.2, 1.8, 1.4)
+
+
+def bushing_mesh(scale: float = 1.0, eps_r: float = 4.0, V0: float = 1.0) -> Mesh:
+    """Graded-foil bushing analogue (the arrangement of Sec. 5's validation case,
+    with made-up dimensions): a high-voltage rod (closed cylinder, radius 0.1,
+    length 5, potential V0) inside five coaxial cylindrical foils, open at both
+    ends, at the radii BUSHING_FOIL_RADII with the lengths BUSHING_FOIL_LENGTHS
+    (centred at z=0).  The outermost foil is grounded (a conductor at 0); the four
+    inner ones are thin floating sheets.  All foils lie in one insulator, so both
+    sides of a sheet have eps_r.  Edge length about 0.06/scale (about 21k
+    triangles at scale 1)."""
+    h = 0.06 / scale
+    K = max(2, int(round(2.0 * np.pi * 0.1 / h / 6.0)))
+    Xr, Tr = closed_cylinder(0.1, 5.0, (0.0, 0.0, 0.0), K, max(2, int(round(5.0 / h))))
+    parts = [(Xr, Tr, 0)]
+    regions = [{"kind": "conductor", "V0": V0}]
+    nf = len(BUSHING_FOIL_RADII)
+    for k, (r, L) in enumerate(zip(BUSHING_FOIL_RADII, BUSHING_FOIL_LENGTHS)):
+        n_t = max(6, int(round(2.0 * np.pi * r / h)))
+        n_z = max(2, int(round(L / h)))
+        Xf, Tf = open_cylinder(r, -L / 2.0, L / 2.0, n_t, n_z)
+        parts.append((Xf, Tf, len(regions)))
+        if k == nf - 1:
+            regions.append({"kind": "conductor", "V0": 0.0})
+        else:
+            regions.append({"kind": "sheet", "floating_id": k, "eps_plus": eps_r, "eps_minus": eps_r})
+    X, tri, region = _merge(parts)
+    info = {"body": "bushing", "scale": scale, "counts": tuple(len(p[1]) for p in parts), "eps_r": eps_r}
     return Mesh(X, tri, region, regions, info)
 
 

@@ -47,3 +47,26 @@ def test_family_jitter_bounded():
     d = np.abs(jit.X - base.X)
     assert (d <= 0.02 * h[:, None] + 1e-15).all()
     assert d.max() > 0.005 * h.max() * 0.1   # it does move
+
+
+def test_open_cylinder_sheet():
+    """An open cylindrical foil: normals point away from the axis, and its two rims
+    are the only boundary (2 n_t edges used by one triangle)."""
+    X, tri = mg.open_cylinder(0.5, -1.0, 1.0, 24, 10)
+    a, b, c = X[tri[:, 0]], X[tri[:, 1]], X[tri[:, 2]]
+    n = np.cross(b - a, c - a)
+    ctr = (a + b + c) / 3.0
+    assert np.all(n[:, 0] * ctr[:, 0] + n[:, 1] * ctr[:, 1] > 0.0)
+    e = np.sort(np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]]), axis=1)
+    _, cnt = np.unique(e, axis=0, return_counts=True)
+    assert np.sum(cnt == 1) == 2 * 24 and np.all(cnt <= 2)
+
+
+def test_bushing_and_sheet_meshes():
+    m = mg.bushing_mesh(1.0)
+    assert 19000 < m.np_ < 23000
+    assert m.n_floating == 4
+    assert [r["kind"] for r in m.regions] == ["conductor"] + ["sheet"] * 4 + ["conductor"]
+    assert m.regions[-1]["V0"] == 0.0
+    s = mg.sphere_in_sheet_mesh(2)
+    assert s.n_floating == 1 and s.regions[1]["eps_minus"] == 4.0
