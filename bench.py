@@ -57,7 +57,7 @@ def parse():
                     help="matvec: only W+K mixed matvecs of the workload (a small case for ncu); "
                          "batch: the uneven device family solved and traced by the batched calls; "
                          "report: per-configuration times and errors of both GPU forms and the oracle")
-    ap.add_argument("--report-configs", default="c1,c2,c3,c5", help="report mode: configurations")
+    ap.add_argument("--report-configs", default="c1,c2,c3,bushing,c5", help="report mode: configurations")
     ap.add_argument("--c5-lines", type=int, default=64, help="report mode: field lines traced on c5")
     ap.add_argument("--lines", type=int, default=512, help="trace mode: field lines")
     ap.add_argument("--max-steps", type=int, default=200000, help="trace mode: RK4 step limit per line")
@@ -685,6 +685,43 @@ def run_report(args):
         (Ko, so, no, xo), t_o = wall(lambda: P.trace(u64[0].cpu().numpy(), mg.fibonacci_seeds(256)[:4]))
         out["oracle"] = {"trace_4_lines_ms": t_o, "trace_256_lines_s_extrapolated": t_o * 64 / 1e3}
         ctx.close()
+        emit(out)
+    if "bushing" in want:
+        # thin floating sheets (Eq. sheets): rod at 1, four floating foils, grounded
+        # outer foil; foil potentials and net charges at ~21k triangles
+        mesh = mg.bushing_mesh(1.0)
+        a_ = mesh.X[mesh.tri[:, 1]] - mesh.X[mesh.tri[:, 0]]
+        b_ = mesh.X[mesh.tri[:, 2]] - mesh.X[mesh.tri[:, 0]]
+        area = 0.5 * np.linalg.norm(np.cross(a_, b_), axis=1)
+        out = {"config": f"bushing analogue, {mesh.np_} triangles (rod, 4 floating foils, grounded foil), "
+                         f"tol {TOL}"}
+        res = {}
+        for name, prec in (("fp64", bem.FP64), ("mixed", bem.MIXED)):
+            ctx, t_set = wall(lambda: bem.Context(mesh))
+            (u, it, rel), t_sol = timed(lambda: ctx.solve(prec, tol=TOL))
+            ug = u[0].cpu().numpy()
+            q = ug[: mesh.np_] * area
+            q_rod = float(np.sum(q[mesh.region == 0]))
+            res[name] = ug
+            out[name] = {"setup_ms": t_set, "solve_ms": t_sol, "iters": it, "relres": rel[0],
+                         "foil_V": [float(v) for v in ug[mesh.np_:]],
+                         "foil_net_charge_over_rod": [float(np.sum(q[mesh.region == f + 1]) / q_rod)
+                                                      for f in range(4)]}
+            ctx.close()
+        out["mixed"]["sigma_rel_l2_vs_fp64"] = float(np.linalg.norm(res["mixed"] - res["fp64"]) /
+                                                     np.linalg.norm(res["fp64"]))
+        small = mg.bushing_mesh(0.25)
+        Ps = O.Problem(small, eta=4.0, g=3)
+        (u_o), t_o = wall(lambda: Ps.solve())
+        ctx = bem.Context(small)
+        u_s, _, _ = ctx.solve(bem.MIXED, tol=1e-10)
+        ctx.close()
+        rate, rows, secs = cpu_oracle_rate(mesh, 8.0)
+        out["oracle"] = {"small_case": f"{small.np_} triangles: assemble + LU {t_o:.0f} ms",
+                         "small_case_foil_V": [float(v) for v in u_o[small.np_:]],
+                         "small_case_mixed_gpu_foil_V": [float(v) for v in u_s[0].cpu().numpy()[small.np_:]],
+                         "pairs_per_s": rate, "sample": f"{rows} rows x {mesh.np_} triangles, {secs:.1f} s",
+                         "one_product_s_extrapolated": mesh.np_ ** 2 / rate}
         emit(out)
     if "c5" in want:
         scale = (200000 / 20068.0) ** 0.5

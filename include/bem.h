@@ -54,8 +54,13 @@ enum {
     BEM_ERR_CAPACITY = -7       /* a size exceeds the workspace fixed at bem_create */
 };
 
-/* Boundary condition of a group of triangles (Sec. 2, Eqs. Final1-Final4). */
-enum { BEM_CONDUCTOR = 0, BEM_FLOATING = 1, BEM_DIELECTRIC = 2 };
+/* Boundary condition of a group of triangles (Sec. 2, Eqs. Final1-Final4).
+ * BEM_SHEET: a thin floating conductive sheet modelled by a single, possibly open
+ * surface (Eq. sheets): potential rows as BEM_FLOATING, neutrality row with the
+ * fields of both sides.  Floating conductors and sheets share the floating ids.
+ * Field lines end on conductor and floating bodies, which must be closed
+ * surfaces; they do not end on sheets. */
+enum { BEM_CONDUCTOR = 0, BEM_FLOATING = 1, BEM_DIELECTRIC = 2, BEM_SHEET = 3 };
 
 /* Arithmetic of the regular (far-field) pairs.  BEM_FP64: every step in FP64.
  * BEM_MIXED: regular pairs in FP32 with compensated FP32 accumulation; the
@@ -66,10 +71,11 @@ enum { BEM_FP64 = 0, BEM_MIXED = 1, BEM_DF = 2 };
 
 typedef struct {
     int32_t kind;        /* BEM_CONDUCTOR, BEM_FLOATING or BEM_DIELECTRIC */
-    int32_t floating_id; /* BEM_FLOATING: 0 .. n_floating-1, one id per floating body */
+    int32_t floating_id; /* BEM_FLOATING, BEM_SHEET: 0 .. n_floating-1, one id per floating body */
     double V0;           /* BEM_CONDUCTOR: prescribed potential (Eq. conductor) */
     double eps_plus;     /* permittivity on the normal's side (Eqs. Jump, Final4, Final3) */
-    double eps_minus;    /* BEM_DIELECTRIC: permittivity on the other side */
+    double eps_minus;    /* BEM_DIELECTRIC, BEM_SHEET: permittivity on the other side
+                            (a sheet may take 0, which gives the closed floating body's row) */
 } bem_region;
 
 typedef struct {
@@ -167,7 +173,9 @@ int bem_reset_counters(bem_ctx* ctx);
  *   floating f: A_ij = S_j(c_i),                      A_{i,N+f} = -1
  *   dielectric: A_ij = (eps+ - eps-) n_i.G_j(c_i) + delta_ij (eps+ + eps-)/2
  * Row N+f (charge neutrality of floating body f, Eq. Final4 by the centroid rule,
- * divided by the body's area):  A_{N+f,j} = sum_{i in f} A_i eps+ (delta_ij/2 + n_i.G_j(c_i)) / area_f.
+ * divided by the body's area):  A_{N+f,j} = sum_{i in f} A_i eps+ (delta_ij/2 + n_i.G_j(c_i)) / area_f;
+ * rows i of a sheet contribute A_i ((eps+ + eps-) delta_ij/2 + (eps+ - eps-) n_i.G_j(c_i)) / area_f
+ * instead (Eq. sheets), area_f being the body's total area.
  * n_i.G_i(c_i) is the principal value, 0 for a flat triangle.
  * A_dev: device, row-major double, (row1-row0) rows of leading dimension lda >= N+F.
  * precision: BEM_FP64 or BEM_MIXED (regular pairs rounded to FP32).

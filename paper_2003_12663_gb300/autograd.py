@@ -21,9 +21,9 @@ def _regions_with(regions, V0, eps):
         R = dict(R)
         if R["kind"] == "conductor":
             R["V0"] = float(V0[r])
-        if R["kind"] in ("floating", "dielectric"):
+        if R["kind"] in ("floating", "dielectric", "sheet"):
             R["eps_plus"] = float(eps[r, 0])
-        if R["kind"] == "dielectric":
+        if R["kind"] in ("dielectric", "sheet"):
             R["eps_minus"] = float(eps[r, 1])
         out.append(R)
     return out

@@ -17,8 +17,8 @@ LIB_PATH = os.path.join(HERE, "libbem.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "bem.h")
 
 FP64, MIXED, DF = 0, 1, 2
-CONDUCTOR, FLOATING, DIELECTRIC = 0, 1, 2
-_KIND = {"conductor": CONDUCTOR, "floating": FLOATING, "dielectric": DIELECTRIC}
+CONDUCTOR, FLOATING, DIELECTRIC, SHEET = 0, 1, 2, 3
+_KIND = {"conductor": CONDUCTOR, "floating": FLOATING, "dielectric": DIELECTRIC, "sheet": SHEET}
 
 ERRORS = {0: "BEM_OK", -1: "BEM_ERR_ARG", -2: "BEM_ERR_CUDA", -3: "BEM_ERR_DEGENERATE",
           -4: "BEM_ERR_NOT_CONVERGED", -5: "BEM_ERR_TIMEOUT", -6: "BEM_ERR_NOMEM",

@@ -577,15 +577,15 @@ k_far_T(int64_t np, const float4* __restrict__ t32, const double4* __restrict__ 
 }
 
 // finish A^T v for columns j < N: far partials + near pairs (column list) +
-// dielectric diagonal + the 1/2 term of the neutrality rows
+// dielectric diagonal + the u_j terms of the neutrality rows (1/2, and a sheet's eps-)
 __global__ void k_finish_T(int64_t np, int splits, const double* __restrict__ part,
                            const int64_t* __restrict__ cptr, const int32_t* __restrict__ crow,
                            const int64_t* __restrict__ cent, const double4* __restrict__ val,
                            const uint8_t* __restrict__ flag, uint8_t bit,
                            const double4* __restrict__ src, const int32_t* __restrict__ kind,
                            const int32_t* __restrict__ aux, const double* __restrict__ ra,
-                           const double* __restrict__ rw, const double* __restrict__ v,
-                           double* __restrict__ y)
+                           const double* __restrict__ rw, const double* __restrict__ rs,
+                           const double* __restrict__ v, double* __restrict__ y)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= np) return;
@@ -599,7 +599,7 @@ __global__ void k_finish_T(int64_t np, int splits, const double* __restrict__ pa
         s += sv.x * vv.x + sv.y * vv.y + sv.z * vv.z + sv.w * vv.w;
     }
     if (kind[j] == BEM_DIELECTRIC) s += ra[j] * v[j];
-    if (kind[j] == BEM_FLOATING) s += 0.5 * rw[j] * v[np + aux[j]];
+    if (kind[j] == BEM_FLOATING) s += (0.5 * rw[j] + rs[j]) * v[np + aux[j]];
     y[j] = s;
 }
 
@@ -727,7 +727,7 @@ __global__ void k_sys_row_terms(int64_t np, int splits_r, int splits_c, const do
                                 const double* __restrict__ rb, const double* __restrict__ rw,
                                 const double* __restrict__ mu, const double* __restrict__ u,
                                 const double* __restrict__ field, const double* __restrict__ Tf,
-                                const double* __restrict__ eps_plus_f, const double* __restrict__ area_f,
+                                const double2* __restrict__ ceps, const double* __restrict__ area_f,
                                 const double* __restrict__ part_r, const double* __restrict__ part_c,
                                 double* __restrict__ gP)
 {
@@ -767,11 +767,12 @@ __global__ void k_sys_row_terms(int64_t np, int splits_r, int splits_c, const do
             out[6 + q] += Pe1[q];
         }
     }
-    if (kind[i] == BEM_FLOATING) {  // neutrality weights A_i eps+ / area_f
+    if (kind[i] == BEM_FLOATING) {  // neutrality weights A_i / area_f of the summands tau_i
         const int f = aux[i];
         const double* E = field + 4 * i + 1;
         const double ti = 0.5 * u[i] + E[0] * gp[GEO_N] + E[1] * gp[GEO_N + 1] + E[2] * gp[GEO_N + 2];
-        const double s = -mu[np + f] * eps_plus_f[f] / area_f[f] * (ti - Tf[f]);
+        const double tau = ceps[i].x * ti + ceps[i].y * u[i];
+        const double s = -mu[np + f] / area_f[f] * (tau - Tf[f]);
         double dA[9];
         area_grad(gp, dA);
         for (int q = 0; q < 9; ++q) out[q] += s * dA[q];
@@ -780,11 +781,13 @@ __global__ void k_sys_row_terms(int64_t np, int splits_r, int splits_c, const do
     for (int q = 0; q < 9; ++q) o[q] += out[q];
 }
 
-// neutrality means T_f = sum_{i in f} A_i t_i / area_f
+// neutrality means T_f = sum_{i in f} A_i tau_i / area_f, with the summand
+// tau_i = ce_i (u_i/2 + (K'u)_i) + em_i u_i: ce = eps+ and em = 0 on a closed
+// floating body, ce = eps+ - eps- and em = eps- on a sheet (Eq. sheets)
 __global__ void k_float_means(int64_t np, const int32_t* __restrict__ rows, const int32_t* __restrict__ off,
                               const double* __restrict__ geo, const double* __restrict__ u,
-                              const double* __restrict__ field, const double* __restrict__ area_f,
-                              double* __restrict__ Tf)
+                              const double* __restrict__ field, const double2* __restrict__ ceps,
+                              const double* __restrict__ area_f, double* __restrict__ Tf)
 {
     __shared__ double sh[256];
     const int f = blockIdx.x;
@@ -793,7 +796,8 @@ __global__ void k_float_means(int64_t np, const int32_t* __restrict__ rows, cons
         const int i = rows[k];
         const double* gp = geo + GEO_STRIDE * i;
         const double* E = field + 4 * i + 1;
-        s += gp[GEO_AREA] * (0.5 * u[i] + E[0] * gp[GEO_N] + E[1] * gp[GEO_N + 1] + E[2] * gp[GEO_N + 2]);
+        const double ti = 0.5 * u[i] + E[0] * gp[GEO_N] + E[1] * gp[GEO_N + 1] + E[2] * gp[GEO_N + 2];
+        s += gp[GEO_AREA] * (ceps[i].x * ti + ceps[i].y * u[i]);
     }
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -809,8 +813,8 @@ __global__ void k_region_grads(int64_t np, int nreg, const int32_t* __restrict__
                                const int32_t* __restrict__ kind, const int32_t* __restrict__ aux,
                                const double* __restrict__ geo, const double* __restrict__ mu,
                                const double* __restrict__ u, const double* __restrict__ field,
-                               const double* __restrict__ area_f, double* __restrict__ gV0,
-                               double* __restrict__ geps)
+                               const double* __restrict__ area_f, const int32_t* __restrict__ sheet,
+                               double* __restrict__ gV0, double* __restrict__ geps)
 {
     __shared__ double sh[3][256];
     const int r = blockIdx.x;
@@ -825,8 +829,10 @@ __global__ void k_region_grads(int64_t np, int nreg, const int32_t* __restrict__
         } else if (kind[i] == BEM_DIELECTRIC) {
             bp += -mu[i] * (0.5 * u[i] + kp);
             bm += -mu[i] * (0.5 * u[i] - kp);
-        } else {
-            bp += -mu[np + aux[i]] * gp[GEO_AREA] / area_f[aux[i]] * (0.5 * u[i] + kp);
+        } else {  // floating body or sheet: the neutrality row's eps terms
+            const double w = -mu[np + aux[i]] * gp[GEO_AREA] / area_f[aux[i]];
+            bp += w * (0.5 * u[i] + kp);
+            if (sheet[r]) bm += w * (0.5 * u[i] - kp);
         }
     }
     sh[0][threadIdx.x] = a; sh[1][threadIdx.x] = bp; sh[2][threadIdx.x] = bm;
@@ -933,7 +939,7 @@ int matvecT_impl(bem_ctx* c, int precision, const double* v, double* y)
     BEM_LAUNCH_CHECK(c);
     k_finish_T<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
         np, splits, c->part, c->csc_ptr, c->csc_row, c->csc_ent, c->near_val, c->near_flag,
-        (uint8_t)(f32 ? 1 : 2), c->tsrc64, c->row_kind, c->row_aux, c->row_a, c->row_w, v, y);
+        (uint8_t)(f32 ? 1 : 2), c->tsrc64, c->row_kind, c->row_aux, c->row_a, c->row_w, c->row_s, v, y);
     BEM_LAUNCH_CHECK(c);
     if (c->nfloat > 0) {
         k_float_cols<<<c->nfloat, 256, 0, s>>>(np, c->float_rows, c->float_off, v, y);
@@ -1030,26 +1036,35 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     rc = matvec_impl(c, precision, 1, A.u, c->wvec, true);  // fills c->field with phi, E_PV at the centroids
     if (rc) return rc;
     const int nreg = (int)c->regions.size();
-    std::vector<double> h_epf(std::max(c->nfloat, 1), 1.0), h_af(std::max(c->nfloat, 1), 0.0);
+    // per row (ce, em) of the neutrality summand (see k_float_means), per region
+    // whether it is a sheet, per floating body its area
+    std::vector<double2> h_ceps(np, make_double2(0.0, 0.0));
+    std::vector<double> h_af(std::max(c->nfloat, 1), 0.0);
+    std::vector<int32_t> h_sheet(nreg, 0);
     {
         std::vector<double> g(GEO_STRIDE * np);
         BEM_CUDA_TRY(c, cudaMemcpyAsync(g.data(), c->geo, g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
         for (int64_t i = 0; i < np; ++i) {
             const bem_region& R = c->regions[c->h_region[i]];
-            if (R.kind == BEM_FLOATING) {
-                h_af[R.floating_id] += g[GEO_STRIDE * i + GEO_AREA];
-                h_epf[R.floating_id] = R.eps_plus;
-            }
+            if (R.kind == BEM_FLOATING || R.kind == BEM_SHEET) h_af[R.floating_id] += g[GEO_STRIDE * i + GEO_AREA];
+            if (R.kind == BEM_FLOATING) h_ceps[i] = make_double2(R.eps_plus, 0.0);
+            if (R.kind == BEM_SHEET) h_ceps[i] = make_double2(R.eps_plus - R.eps_minus, R.eps_minus);
         }
+        for (int r = 0; r < nreg; ++r) h_sheet[r] = c->regions[r].kind == BEM_SHEET;
     }
-    DevBuf<double> epf, af, Tf, gPs;
-    if (epf.alloc(h_epf.size()) || af.alloc(h_af.size()) || Tf.alloc(h_af.size()) || gPs.alloc(9 * np))
+    DevBuf<double2> ceps;
+    DevBuf<double> af, Tf, gPs;
+    DevBuf<int32_t> sheet;
+    if (ceps.alloc(np) || af.alloc(h_af.size()) || Tf.alloc(h_af.size()) || gPs.alloc(9 * np) ||
+        sheet.alloc(nreg))
         return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(epf.p, h_epf.data(), h_epf.size() * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(ceps.p, h_ceps.data(), np * sizeof(double2), cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(af.p, h_af.data(), h_af.size() * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(sheet.p, h_sheet.data(), nreg * 4, cudaMemcpyHostToDevice, s));
     if (c->nfloat > 0) {
-        k_float_means<<<c->nfloat, 256, 0, s>>>(np, c->float_rows, c->float_off, c->geo, A.u, c->field, af.p, Tf.p);
+        k_float_means<<<c->nfloat, 256, 0, s>>>(np, c->float_rows, c->float_off, c->geo, A.u, c->field, ceps.p,
+                                                af.p, Tf.p);
         BEM_LAUNCH_CHECK(c);
     }
     const int64_t tiles = (np + 127) / 128;
@@ -1070,10 +1085,10 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     BEM_CUDA_TRY(c, cudaMemcpyAsync(gPs.p, gPt.p, 9 * np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     k_sys_row_terms<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(
         np, splits, splits, c->geo, c->row_kind, c->row_aux, c->row_b, c->row_w, mu.p, A.u, c->field,
-        Tf.p, epf.p, af.p, pr.p, pc.p, gPs.p);
+        Tf.p, ceps.p, af.p, pr.p, pc.p, gPs.p);
     BEM_LAUNCH_CHECK(c);
     k_region_grads<<<nreg, 256, 0, s>>>(np, nreg, c->d_region, c->row_kind, c->row_aux, c->geo, mu.p,
-                                         A.u, c->field, af.p, gV0, geps);
+                                         A.u, c->field, af.p, sheet.p, gV0, geps);
     BEM_LAUNCH_CHECK(c);
     if (gX) {
         // vertex -> (triangle, corner) lists

@@ -55,6 +55,7 @@ struct Inst {  // one mesh, device view
     const double* ra;
     const double* rb;
     const double* rw;
+    const double* rs;
     const double* jinv;
     const int32_t* frows;
     const int32_t* foff;
@@ -276,7 +277,8 @@ __global__ void k_brows(const Inst* __restrict__ insts, const Sys* __restrict__ 
     else if (kd == BEM_FLOATING) yi = p - x[np + I.aux[i]];   // Eq. Final2
     else yi = I.ra[i] * x[i] + I.rb[i] * en;                  // Eq. Final3
     S.vec[V_W][i] = yi;
-    S.vec[V_NEUT][i] = kd == BEM_FLOATING ? I.rw[i] * (0.5 * x[i] + en) : 0.0;  // Eq. Final4 summand
+    // Eq. Final4 summand (Eq. sheets for the rows of a sheet: rs_i != 0)
+    S.vec[V_NEUT][i] = kd == BEM_FLOATING ? I.rw[i] * (0.5 * x[i] + en) + I.rs[i] * x[i] : 0.0;
 }
 
 // neutrality rows (Eq. Final4), one block per system, fixed summation order
@@ -743,6 +745,7 @@ extern "C" int bem_batch_create(bem_batch** out, bem_ctx* const* ctxs, int32_t n
         I.tgt32 = c->tgt32; I.hdr32 = c->hdr32; I.node32 = c->node32; I.geo = c->geo;
         I.near_ptr = c->near_ptr; I.near_col = c->near_col; I.near_val = c->near_val; I.near_flag = c->near_flag;
         I.kind = c->row_kind; I.aux = c->row_aux; I.ra = c->row_a; I.rb = c->row_b; I.rw = c->row_w;
+        I.rs = c->row_s;
         I.jinv = c->jinv;
         I.frows = c->float_rows; I.foff = c->float_off; I.nfloat = c->nfloat;
         ok = dalloc(b, &I.part, (size_t)nr * I.splits * I.np * 4);

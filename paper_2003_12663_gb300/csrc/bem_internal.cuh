@@ -64,10 +64,11 @@ struct bem_ctx {
     int32_t* row_aux = nullptr;    // [np] floating id or region index of a conductor
     double* row_a = nullptr;       // [np] dielectric: (eps+ + eps-)/2
     double* row_b = nullptr;       // [np] dielectric: eps+ - eps-
-    double* row_w = nullptr;       // [np] floating: A_i eps+ / area_f
+    double* row_w = nullptr;       // [np] floating: A_i eps+ / area_f; sheet: A_i (eps+ - eps-) / area_f
+    double* row_s = nullptr;       // [np] sheet: A_i eps- / area_f (0 elsewhere)
     double* region_V0 = nullptr;   // [nregions]
     int32_t* d_region = nullptr;   // [np] region of every triangle
-    int32_t* d_electrode = nullptr;  // [nregions] 1 for conductor and floating regions
+    int32_t* d_electrode = nullptr;  // [nregions] 1 for conductor and floating regions (not sheets)
     int32_t* float_rows = nullptr; // rows of every floating body, grouped
     int32_t* float_off = nullptr;  // [nfloat+1]
     double* jinv = nullptr;        // [nunk] inverse Jacobi diagonal

@@ -22,8 +22,8 @@ __global__ void k_rows(int64_t np, int splits, const double* __restrict__ part,
                        uint8_t bit, const double* __restrict__ x, const double* __restrict__ geo,
                        const int32_t* __restrict__ kind, const int32_t* __restrict__ aux,
                        const double* __restrict__ ra, const double* __restrict__ rb,
-                       const double* __restrict__ rw, int mode, double* __restrict__ y,
-                       double* __restrict__ neut, double* __restrict__ field)
+                       const double* __restrict__ rw, const double* __restrict__ rs, int mode,
+                       double* __restrict__ y, double* __restrict__ neut, double* __restrict__ field)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -69,7 +69,8 @@ __global__ void k_rows(int64_t np, int splits, const double* __restrict__ part,
         yi = ra[i] * x[i] + rb[i] * en;           // Eq. Final3
     }
     y[i] = yi;
-    neut[i] = (kd == BEM_FLOATING) ? rw[i] * (0.5 * x[i] + en) : 0.0;  // Eq. Final4 summand
+    // Eq. Final4 summand (Eq. sheets for the rows of a sheet: rs_i != 0)
+    neut[i] = (kd == BEM_FLOATING) ? rw[i] * (0.5 * x[i] + en) + rs[i] * x[i] : 0.0;
 }
 
 // One block per floating body: y[N+f] = sum of its rows' neutrality terms, in a
@@ -267,7 +268,8 @@ __global__ void k_assemble_neutral(int f, int64_t np, const int32_t* __restrict_
                                    const double4* __restrict__ node64, const double* __restrict__ geo,
                                    const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                    const double4* __restrict__ val, const uint8_t* __restrict__ flag,
-                                   uint8_t bit, const double* __restrict__ rw, double* __restrict__ out)
+                                   uint8_t bit, const double* __restrict__ rw,
+                                   const double* __restrict__ rs, double* __restrict__ out)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= np) return;
@@ -321,6 +323,7 @@ __global__ void k_assemble_neutral(int f, int64_t np, const int32_t* __restrict_
         double en = gx * gi[GEO_N] + gy * gi[GEO_N + 1] + gz * gi[GEO_N + 2];
         if (j == i) en += 0.5;
         acc += rw[i] * en;
+        if (j == i) acc += rs[i];  // a sheet's eps- u_i term (Eq. sheets)
     }
     out[j] = acc;
 }
@@ -365,7 +368,7 @@ int assemble_dispatch(bem_ctx* c, int64_t row0, int64_t row1, double* A, int64_t
 #define ASM_NEU(QQ)                                                                             \
     k_assemble_neutral<F32, QQ><<<(unsigned)((np + 127) / 128), 128, 0, s>>>(                    \
         f, np, c->float_rows, c->float_off, c->tgt32, c->tgt64, c->hdr32, c->hdr64, c->node32,  \
-        c->node64, c->geo, c->near_ptr, c->near_col, c->near_val, c->near_flag, bit, c->row_w, out)
+        c->node64, c->geo, c->near_ptr, c->near_col, c->near_val, c->near_flag, bit, c->row_w, c->row_s, out)
         switch (c->g) {
             case 1: ASM_NEU(1); break;
             case 2: ASM_NEU(4); break;
@@ -401,7 +404,7 @@ int matvec_impl(bem_ctx* c, int precision, int nrhs, const double* x, double* y,
         const double* pr = c->part + (size_t)r * splits * np * 4;
         k_rows<<<(unsigned)((np * 32 + 127) / 128), 128, 0, c->stream>>>(
             np, splits, pr, c->near_ptr, c->near_col, nval, c->near_flag, bit, x + r * n,
-            c->geo, c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, 0, y + r * n,
+            c->geo, c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, c->row_s, 0, y + r * n,
             c->neut + r * np, c->field + (size_t)r * np * 4);
         BEM_LAUNCH_CHECK(c);
         if (c->nfloat > 0) {
@@ -456,7 +459,7 @@ extern "C" int bem_surface_field(bem_ctx* c, int32_t precision, const double* u,
     const uint8_t bit = precision == BEM_MIXED ? 1 : 2;
     k_rows<<<(unsigned)((np * 32 + 127) / 128), 128, 0, c->stream>>>(
         np, splits, c->part, c->near_ptr, c->near_col, c->near_val, c->near_flag, bit, u, c->geo,
-        c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, 1, E, nullptr, nullptr);
+        c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, c->row_s, 1, E, nullptr, nullptr);
     BEM_LAUNCH_CHECK(c);
     return BEM_OK;
 }

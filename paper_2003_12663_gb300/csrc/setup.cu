@@ -384,7 +384,7 @@ static void free_ctx(bem_ctx* c)
     if (!c) return;
     void* ptrs[] = {c->X, c->tri, c->geo, c->hdr32, c->hdr64, c->node32, c->node64, c->tgt32,
                     c->tgt64, c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, c->region_V0,
-                    c->float_rows, c->float_off, c->jinv, c->near_ptr, c->near_col, c->near_val,
+                    c->row_s, c->float_rows, c->float_off, c->jinv, c->near_ptr, c->near_col, c->near_val,
                     c->near_flag, c->part, c->field, c->neut, c->pts_stage, c->V, c->wvec,
                     c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
                     c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df, c->d_region,
@@ -655,7 +655,7 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     // rows
     const int nreg = (int)c->regions.size();
     std::vector<int32_t> kind(np), aux(np);
-    std::vector<double> ra(np, 0.0), rb(np, 0.0), rw(np, 0.0), V0(nreg, 0.0);
+    std::vector<double> ra(np, 0.0), rb(np, 0.0), rw(np, 0.0), rs(np, 0.0), V0(nreg, 0.0);
     std::vector<double> area_f(c->nfloat, 0.0);
     std::vector<std::vector<int32_t>> frows(c->nfloat);
     std::vector<double> h_area(np);
@@ -667,14 +667,21 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         for (int64_t i = 0; i < np; ++i) h_area[i] = g[GEO_STRIDE * i + GEO_AREA];
     }
     for (int r = 0; r < nreg; ++r) V0[r] = c->regions[r].kind == BEM_CONDUCTOR ? c->regions[r].V0 : 0.0;
+    // A sheet's rows are those of a floating conductor; only its neutrality
+    // summand differs (Eq. sheets): the closed body's is A_i eps+ (u_i/2 + (K'u)_i),
+    // the sheet's A_i ((eps+ + eps-)/2 u_i + (eps+ - eps-)(K'u)_i), both over area_f.
+    // Both are written rw_i (u_i/2 + (K'u)_i) + rs_i u_i, with
+    // rw_i = A_i (eps+ - eps-) / area_f and rs_i = A_i eps- / area_f, where a
+    // closed body has eps- = 0 (no displacement field inside a conductor).
     for (int64_t i = 0; i < np; ++i) {
         const bem_region& R = c->regions[c->h_region[i]];
-        kind[i] = R.kind;
-        aux[i] = R.kind == BEM_FLOATING ? R.floating_id : c->h_region[i];
+        const bool fl = R.kind == BEM_FLOATING || R.kind == BEM_SHEET;
+        kind[i] = fl ? BEM_FLOATING : R.kind;
+        aux[i] = fl ? R.floating_id : c->h_region[i];
         if (R.kind == BEM_DIELECTRIC) {
             ra[i] = 0.5 * (R.eps_plus + R.eps_minus);
             rb[i] = R.eps_plus - R.eps_minus;
-        } else if (R.kind == BEM_FLOATING) {
+        } else if (fl) {
             area_f[R.floating_id] += h_area[i];
             frows[R.floating_id].push_back((int32_t)i);
         }
@@ -682,6 +689,10 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     for (int64_t i = 0; i < np; ++i) {
         const bem_region& R = c->regions[c->h_region[i]];
         if (R.kind == BEM_FLOATING) rw[i] = h_area[i] * R.eps_plus / area_f[R.floating_id];
+        if (R.kind == BEM_SHEET) {
+            rw[i] = h_area[i] * (R.eps_plus - R.eps_minus) / area_f[R.floating_id];
+            rs[i] = h_area[i] * R.eps_minus / area_f[R.floating_id];
+        }
     }
     std::vector<int32_t> fr, fo(c->nfloat + 1, 0);
     for (int f = 0; f < c->nfloat; ++f) {
@@ -690,7 +701,8 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     }
     if ((rc = dalloc(c, &c->row_kind, np)) || (rc = dalloc(c, &c->row_aux, np)) ||
         (rc = dalloc(c, &c->row_a, np)) || (rc = dalloc(c, &c->row_b, np)) ||
-        (rc = dalloc(c, &c->row_w, np)) || (rc = dalloc(c, &c->region_V0, nreg)) ||
+        (rc = dalloc(c, &c->row_w, np)) || (rc = dalloc(c, &c->row_s, np)) ||
+        (rc = dalloc(c, &c->region_V0, nreg)) ||
         (rc = dalloc(c, &c->float_rows, fr.size())) || (rc = dalloc(c, &c->float_off, fo.size())) ||
         (rc = dalloc(c, &c->jinv, c->nunk)))
         return rc;
@@ -699,8 +711,10 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->row_a, ra.data(), np * 8, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->row_b, rb.data(), np * 8, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->row_w, rw.data(), np * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(c->row_s, rs.data(), np * 8, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(c, cudaMemcpyAsync(c->region_V0, V0.data(), nreg * 8, cudaMemcpyHostToDevice, s));
     {
+        // bodies whose surface ends a field line; a thin sheet has no inside
         std::vector<int32_t> elec(nreg);
         for (int r = 0; r < nreg; ++r)
             elec[r] = (c->regions[r].kind == BEM_CONDUCTOR || c->regions[r].kind == BEM_FLOATING) ? 1 : 0;
@@ -786,14 +800,16 @@ extern "C" int bem_create(bem_ctx** out, const bem_mesh* mesh, const bem_params*
     int nfloat = 0;
     for (int r = 0; r < mesh->nregions; ++r) {
         const bem_region& R = mesh->regions[r];
-        if (R.kind < BEM_CONDUCTOR || R.kind > BEM_DIELECTRIC)
+        if (R.kind < BEM_CONDUCTOR || R.kind > BEM_SHEET)
             return set_err(nullptr, BEM_ERR_ARG, "region %d: unknown kind %d", r, R.kind);
-        if (R.kind == BEM_FLOATING) {
+        if (R.kind == BEM_FLOATING || R.kind == BEM_SHEET) {
             if (R.floating_id < 0 || R.floating_id >= mesh->nregions)
                 return set_err(nullptr, BEM_ERR_ARG, "region %d: bad floating_id", r);
             nfloat = std::max(nfloat, R.floating_id + 1);
             if (!(R.eps_plus > 0.0)) return set_err(nullptr, BEM_ERR_ARG, "region %d: eps_plus <= 0", r);
         }
+        if (R.kind == BEM_SHEET && !(R.eps_minus >= 0.0))
+            return set_err(nullptr, BEM_ERR_ARG, "region %d: sheet eps_minus < 0", r);
         if (R.kind == BEM_DIELECTRIC && (!(R.eps_plus > 0.0) || !(R.eps_minus > 0.0)))
             return set_err(nullptr, BEM_ERR_ARG, "region %d: permittivities must be > 0", r);
     }
@@ -802,7 +818,8 @@ extern "C" int bem_create(bem_ctx** out, const bem_mesh* mesh, const bem_params*
         const int r = mesh->region[i];
         if (r < 0 || r >= mesh->nregions)
             return set_err(nullptr, BEM_ERR_ARG, "region index out of range at triangle %lld", (long long)i);
-        if (mesh->regions[r].kind == BEM_FLOATING) seen[mesh->regions[r].floating_id] = 1;
+        if (mesh->regions[r].kind == BEM_FLOATING || mesh->regions[r].kind == BEM_SHEET)
+            seen[mesh->regions[r].floating_id] = 1;
     }
     for (int f = 0; f < nfloat; ++f)
         if (!seen[f]) return set_err(nullptr, BEM_ERR_ARG, "floating id %d has no triangles", f);

@@ -140,6 +140,22 @@ def test_adjoint_floating(bem, oracle_mod):
     run_case(bem, oracle_mod, mesh, seeds, 10, 2, [(0, "V0", 0)])
 
 
+def test_adjoint_sheet(bem, oracle_mod):
+    """Conductor sphere and an open floating sheet (a short cylindrical foil) beside
+    it, with different permittivities on its two sides (Eq. sheets): vertex
+    gradients and dJ/d eps+, dJ/d eps- of the sheet against differences.  The
+    lines leave away from the foil."""
+    regions = [{"kind": "conductor", "V0": 1.0},
+               {"kind": "sheet", "floating_id": 0, "eps_plus": 1.0, "eps_minus": 3.0}]
+    Xf, Tf = mg.open_cylinder(0.4, -0.5, 0.5, 12, 4)
+    mesh = _combine([(mg.icosphere(2, 1.0), 0), ((Xf + np.array([2.5, 0.0, 0.0]), Tf), 1)], regions)
+    seeds = mg.fibonacci_seeds(16)
+    seeds = seeds[seeds[:, 0] < -0.2]
+    gX, gV0, geps = run_case(bem, oracle_mod, mesh, seeds, 10, 2,
+                             [(0, "V0", 0), (1, "eps_plus", 0), (1, "eps_minus", 1)])
+    assert geps[1, 0] != 0.0 and geps[1, 1] != 0.0
+
+
 @pytest.mark.slow
 def test_adjoint_config3(bem):
     """The configuration the gradient is specified on: 1280-triangle sphere at V0=1,

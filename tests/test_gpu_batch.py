@@ -118,6 +118,36 @@ def test_batch_solve_vs_oracle(fam, bem):
     B.close()
 
 
+def test_batch_with_sheets_vs_oracle(bem, oracle_mod):
+    """Instances with thin floating sheets (Eq. sheets): the batched product and
+    solve against the oracle, four right-hand sides."""
+    meshes = [mg.sphere_in_sheet_mesh(2), mg.bushing_mesh(0.25)]
+    ctxs = [bem.Context(m) for m in meshes]
+    probs = [oracle_mod.Problem(m, eta=c.params.eta, g=c.params.far_order) for m, c in zip(meshes, ctxs)]
+    mats = [P.assemble() for P in probs]
+    nr = 4
+    rng = np.random.default_rng(7)
+    xs = [rng.standard_normal((nr, c.nunk)) for c in ctxs]
+    B = bem.Batch(ctxs, nrhs=nr)
+    ys = B.matvec([torch.tensor(x) for x in xs])
+    for x, y, A in zip(xs, ys, mats):
+        yg = y.cpu().numpy()
+        for r in range(nr):
+            ref = A @ x[r]
+            assert np.abs(yg[r] - ref).max() / np.abs(ref).max() < 2e-6
+    V0 = _V0s(meshes, nr)
+    us, iters, rel = B.solve([torch.tensor(v) for v in V0], tol=1e-10)
+    assert (rel <= 1e-10).all(), rel
+    for k, (u, P, A, V) in enumerate(zip(us, probs, mats, V0)):
+        ug = u.cpu().numpy()
+        for r in range(nr):
+            ref = np.linalg.solve(A, _rhs_oracle(P, V[r]))
+            assert np.linalg.norm(ug[r] - ref) / np.linalg.norm(ref) < 1e-6, (k, r)
+    B.close()
+    for c in ctxs:
+        c.close()
+
+
 def test_batch_solve_matches_single(fam, bem):
     """Per system, the batched solve reaches the single-mesh bem_solve's solution."""
     meshes, ctxs, probs, mats = fam

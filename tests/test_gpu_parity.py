@@ -32,6 +32,10 @@ def bem():
 MESHES = {
     "sphere_l3": lambda: mg.sphere_mesh(3),
     "device_s03": lambda: mg.device_mesh(scale=0.3),
+    # thin floating sheets (Eq. sheets): a closed sheet with a permittivity jump
+    # around a conductor sphere, and open foils with a grounded open foil
+    "sheet_sphere_l3": lambda: mg.sphere_in_sheet_mesh(3),
+    "bushing_s025": lambda: mg.bushing_mesh(0.25),
 }
 
 
