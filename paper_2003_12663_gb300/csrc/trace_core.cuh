@@ -130,18 +130,29 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// issue the copies of triangles [c0, c0 + n) into buffer b
+// issue the copies of the calling warp's triangles of the chunk [c0, c0 + n) into
+// buffer b: thread t of the CTA evaluates triangle c0 + t, so warp w reads only
+// triangles w*32 .. w*32+31 of each chunk, and copies exactly those (coalesced).
+// The ring is thus private to each warp: a warp waits for its own copies and
+// synchronises with its own lanes, never with the other warps of the CTA.
 template <int Q>
 __device__ __forceinline__ void stage_chunk(const TArgs& A, Stage32<Q>& S, int b, int64_t c0, int n)
 {
-    const float4* gn = A.node32 + c0 * Q;
-    for (int k = threadIdx.x; k < n * Q; k += kLT) cp_async16(&S.node[b][k], gn + k);
-    for (int k = threadIdx.x; k < n; k += kLT) {
-        cp_async16(&S.hdr[b][k], A.hdr32 + c0 + k);
-        cp_async16(&S.nrm[b][k], A.nrm32 + c0 + k);
+    const int lane = threadIdx.x & 31;
+    const int k0 = (threadIdx.x >> 5) * 32;
+    const int nk = min(n - k0, 32);
+    if (nk <= 0) return;
+    const float4* gn = A.node32 + (c0 + k0) * Q;
+    float4* sn = &S.node[b][k0 * Q];
+    for (int k = lane; k < nk * Q; k += 32) cp_async16(sn + k, gn + k);
+    if (lane < nk) {
+        cp_async16(&S.hdr[b][k0 + lane], A.hdr32 + c0 + k0 + lane);
+        cp_async16(&S.nrm[b][k0 + lane], A.nrm32 + c0 + k0 + lane);
     }
-    for (int k = threadIdx.x; k < n / 4; k += kLT) cp_async16(&S.u[b][4 * k], A.u32 + c0 + 4 * k);
-    for (int k = (n / 4) * 4 + threadIdx.x; k < n; k += kLT) S.u[b][k] = A.u32[c0 + k];
+    // u: 16-byte copies of four values (c0 + k0 is a multiple of 32), plain loads for the rest
+    const int n4 = nk / 4;
+    if (lane < n4) cp_async16(&S.u[b][k0 + 4 * lane], A.u32 + c0 + k0 + 4 * lane);
+    if (4 * n4 + lane < nk) S.u[b][k0 + 4 * n4 + lane] = A.u32[c0 + k0 + 4 * n4 + lane];
 }
 
 // The field at the posted points (slots 0..nt-1: the posting warps in order; NT is
@@ -216,7 +227,8 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
         constexpr int NS = Stage32<Q>::NS;
         const int64_t nch = (A.np + TC - 1) / TC;
         const int t = threadIdx.x;
-        // prologue: chunks 0 .. NS-2 in flight (one commit group per chunk, empty past the end)
+        // prologue: chunks 0 .. NS-2 in flight (one commit group per chunk, empty past the end);
+        // the previous round's reads of the ring ended before the round's entry barrier
 #pragma unroll
         for (int p = 0; p < NS - 1; ++p) {
             if (p < nch) stage_chunk<Q>(A, S, p, (int64_t)p * TC, (int)min((int64_t)TC, A.np - (int64_t)p * TC));
@@ -224,8 +236,8 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
         }
         for (int64_t c = 0; c < nch; ++c) {
             const int b = (int)(c % NS);
-            cp_async_wait<NS - 2>();  // chunks 0..c have landed (NS-2 newer groups may be in flight)
-            cta_bar();                // ... for every thread; and every thread is done with chunk c-1
+            cp_async_wait<NS - 2>();  // this lane's copies of chunks 0..c have landed (NS-2 newer groups may be in flight)
+            __syncwarp();             // ... for every lane of the warp; and every lane is done with chunk c-1
             const int64_t cn = c + NS - 1;  // its buffer, (c-1) % NS, takes chunk c+NS-1 now
             if (cn < nch) stage_chunk<Q>(A, S, (int)(cn % NS), cn * TC, (int)min((int64_t)TC, A.np - cn * TC));
             cp_async_commit();
