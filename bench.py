@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GMRES solve+field-eval time & Ginteractions/s, FP64 vs mixed on GB300 at rel err 1e-6"
 UNIT = "Ginteractions/s"
-FLOPS_PER_PAIR_OP = 18        # phi+E per (target, quadrature node): 3 sub, 5 for r^2, w/r, phi+=, 1/r^2, w/r^3 (2), 3 fma for E
+FLOPS_PER_PAIR_OP = 18        # phi+E per (target, quadrature node): 3 sub, 5 for r^2, w/r, phi+=, 1/r^2, w/r^3, 6 in the 3 fma of E
 PHI_FLOPS_PER_PAIR_OP = 10    # phi alone: 3 sub, 5 for r^2, w/r, phi+=
 FP32_LANES_PER_SM = 128
 TOL = 1e-8
