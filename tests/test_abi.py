@@ -58,3 +58,53 @@ def test_bad_mesh_rejected_before_device(L):
     tri[0, 2] = 2
     assert L.bem_create(ctypes.byref(h), ctypes.byref(m), ctypes.byref(p), None) == -1
     assert b"eta" in L.bem_last_error(None)
+
+
+def test_region_kinds_match_header():
+    """The binding's region kinds are the header's enum values."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(build.__file__), "..", "include", "bem.h")).read()
+    vals = dict((k, int(v)) for k, v in re.findall(r"BEM_(CONDUCTOR|FLOATING|DIELECTRIC|SHEET) = (\d+)", hdr))
+    assert vals == {"CONDUCTOR": bem.CONDUCTOR, "FLOATING": bem.FLOATING,
+                    "DIELECTRIC": bem.DIELECTRIC, "SHEET": bem.SHEET}
+    assert bem._KIND["sheet"] == bem.SHEET
+
+
+def test_bad_regions_rejected_before_device(L):
+    """Region descriptors are checked before any device work: an unknown kind, a
+    sheet with eps- < 0 or a floating id out of range, and a floating id that no
+    triangle carries."""
+    import numpy as np
+    X = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    tri = np.array([[0, 1, 2], [0, 1, 3]], np.int32)
+    reg = np.array([0, 1], np.int32)
+
+    def create(r1, r0=None):
+        regs = (bem.bem_region * 2)()
+        regs[0].kind, regs[0].V0 = bem.CONDUCTOR, 1.0
+        if r0:
+            for k, v in r0.items():
+                setattr(regs[0], k, v)
+        for k, v in r1.items():
+            setattr(regs[1], k, v)
+        m = bem.bem_mesh(4, 2, X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         tri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                         reg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 2, regs)
+        h = ctypes.c_void_p()
+        rc = L.bem_create(ctypes.byref(h), ctypes.byref(m), None, None)
+        assert not h.value
+        return rc, L.bem_last_error(None)
+
+    rc, msg = create({"kind": 4})
+    assert rc == -1 and b"unknown kind" in msg
+    rc, msg = create({"kind": bem.SHEET, "floating_id": 0, "eps_plus": 1.0, "eps_minus": -1.0})
+    assert rc == -1 and b"eps_minus" in msg
+    rc, msg = create({"kind": bem.SHEET, "floating_id": 7, "eps_plus": 1.0, "eps_minus": 1.0})
+    assert rc == -1 and b"floating_id" in msg
+    rc, msg = create({"kind": bem.SHEET, "floating_id": 0, "eps_plus": 0.0, "eps_minus": 1.0})
+    assert rc == -1 and b"eps_plus" in msg
+    # floating id 1 is used by a region that no triangle carries, id 0 by none at all
+    rc, msg = create({"kind": bem.CONDUCTOR, "V0": 0.0},
+                     {"kind": bem.SHEET, "floating_id": 1, "eps_plus": 1.0, "eps_minus": 1.0})
+    assert rc == -1 and b"no triangles" in msg
