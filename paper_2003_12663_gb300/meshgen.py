@@ -292,6 +292,36 @@ def open_cylinder(radius: float, z0: float, z1: float, n_t: int, n_z: int):
     return X, _orient_outward(X, tri, outward).astype(np.int32)
 
 
+def quadratic_from_flat(X: np.ndarray, tri: np.ndarray, project=None):
+    """Six-node (quadratic) triangles from a flat mesh: the corner nodes are the
+    vertices X (indices 0 .. nv-1, unchanged), followed by one node per edge at the
+    edge's midpoint, moved by project(points) -> points if given (e.g. onto a
+    sphere).  Returns (nodes, tri6) with tri6 [N][6] = (v0, v1, v2, m01, m12, m20)."""
+    tri = np.asarray(tri, dtype=np.int64)
+    e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
+    key = np.sort(e, axis=1)
+    uniq, inv = np.unique(key, axis=0, return_inverse=True)
+    mid = 0.5 * (X[uniq[:, 0]] + X[uniq[:, 1]])
+    if project is not None:
+        mid = project(mid)
+    n = len(tri)
+    inv = inv.reshape(-1)
+    m01, m12, m20 = inv[:n], inv[n:2 * n], inv[2 * n:]
+    nv = len(X)
+    tri6 = np.column_stack([tri, nv + m01, nv + m12, nv + m20]).astype(np.int32)
+    return np.concatenate([X, mid]), tri6
+
+
+def quadratic_sphere(level: int, radius: float = 1.0):
+    """Icosphere of the given subdivision level as six-node triangles whose edge
+    nodes lie on the sphere (piecewise quadratic parametrisation of Sec. 3).
+    Returns (nodes, tri6, nv): the first nv nodes are the triangle corners."""
+    X, tri = icosphere(level, radius)
+    nodes, tri6 = quadratic_from_flat(
+        X, tri, lambda p: radius * p / np.linalg.norm(p, axis=1, keepdims=True))
+    return nodes, tri6, len(X)
+
+
 def jitter(X: np.ndarray, tri: np.ndarray, frac: float, seed: int, movable=None) -> np.ndarray:
     """Move each vertex by U(-frac, frac) * (mean length of its edges), per coordinate."""
     rng = np.random.default_rng(seed)
