@@ -24,7 +24,8 @@ What it computes (paper sections / equations):
   with a Gauss rule collapsed at a corner; singular pairs collapsed at the
   collocation point's corner; near-singular pairs after splitting the triangle at
   its point closest to the collocation point, each part collapsed at that point;
-* conductor rows (Eq. Final1): sum_j v_ij u_j = V0, solved by LU (numpy/LAPACK).
+* conductor rows (Eq. Final1): sum_j v_ij u_j = V0, solved by LU (numpy/LAPACK);
+* phi and E of sigma_h at points off the surface (field formula, end of Sec. 2).
 
 The quadrature orders are not stated in the paper; the defaults here (eta = 2 with
 a 12x12 regular rule, 24x24 singular, near-singular 16 points per radial piece and
@@ -154,7 +155,7 @@ def closest_point(x, P6, iters: int = 30):
 
 
 def pair_integrals(x, P6, kind: str, corner: int = -1, g: int = 8, n: int = 24,
-                   n_near=(16, 64)):
+                   n_near=(16, 64), want_G: bool = False):
     """(3,) vector: int lambda_k(y) / (4 pi |x - y|) dS_y over the curved triangle
     P6, for its three mapped linear functions lambda_k.
       kind "regular":  Duffy rule of order g collapsed at corner 0;
@@ -162,7 +163,10 @@ def pair_integrals(x, P6, kind: str, corner: int = -1, g: int = 8, n: int = 24,
       kind "near":     split at the point closest to x, each part collapsed there,
                        its radial variable refined geometrically toward that point
                        down to a tenth of the distance over the triangle's size
-                       (n_near = points per radial piece, angular points)."""
+                       (n_near = points per radial piece, angular points).
+    With want_G (x off the triangle: regular or near kinds), also the (3, 3)
+    array G[k] = int lambda_k(y) (x - y) / (4 pi |x - y|^3) dS_y, the field of
+    each basis function (the field formula at the end of Sec. 2)."""
     if kind == "regular":
         parts = [(CORNERS[0], CORNERS[1], CORNERS[2], g)]
     elif kind == "singular":
@@ -175,6 +179,7 @@ def pair_integrals(x, P6, kind: str, corner: int = -1, g: int = 8, n: int = 24,
         size = np.max(np.linalg.norm(P6[:3] - yp[0], axis=1))
         s_min = 0.1 * np.linalg.norm(x - yp[0]) / size
     out = np.zeros(3)
+    G = np.zeros((3, 3))
     for P0, P1, P2, order in parts:
         if kind == "near":
             xi, eta, w = duffy_graded(P0, P1, P2, n_near[0], s_min, n_near[1])
@@ -185,8 +190,14 @@ def pair_integrals(x, P6, kind: str, corner: int = -1, g: int = 8, n: int = 24,
             continue
         xi, eta, w = xi[keep], eta[keep], w[keep]
         y, J = surface(P6, xi, eta)
-        r = np.linalg.norm(x - y, axis=1)
-        out += (w * J / r) @ linear(xi, eta)
+        d = x - y
+        r = np.linalg.norm(d, axis=1)
+        lam = linear(xi, eta)
+        out += (w * J / r) @ lam
+        if want_G:
+            G += lam.T @ ((w * J / r ** 3)[:, None] * d)
+    if want_G:
+        return out / FOUR_PI, G / FOUR_PI
     return out / FOUR_PI
 
 
@@ -238,6 +249,34 @@ class CurvedProblem:
         if V is None:
             V = self.matrix()
         return np.linalg.solve(V, np.full(self.nv, V0))
+
+    def field(self, u, pts):
+        """phi and E at points off the surface (the field formula at the end of
+        Sec. 2) for vertex values u: every (point, triangle) pair by the regular
+        rule if D > eta R, else by the near-singular rule."""
+        pts = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
+        phi = np.zeros(len(pts))
+        E = np.zeros((len(pts), 3))
+        xi, eta, w = duffy(CORNERS[0], CORNERS[1], CORNERS[2], self.g)
+        lam = linear(xi, eta)
+        for T in range(self.N):
+            P6 = self.nodes[self.tri6[T]]
+            uT = u[self.tri6[T, :3]]
+            cc, R = circumcircle(P6[0], P6[1], P6[2])
+            reg = np.linalg.norm(pts - cc, axis=1) > self.eta * R
+            y, J = surface(P6, xi, eta)
+            dens = w * J * (lam @ uT)
+            idx = np.where(reg)[0]
+            if len(idx):
+                d = pts[idx, None, :] - y[None, :, :]
+                r = np.linalg.norm(d, axis=2)
+                phi[idx] += (dens[None, :] / r).sum(axis=1) / FOUR_PI
+                E[idx] += np.einsum("pq,pqc->pc", dens[None, :] / r ** 3, d) / FOUR_PI
+            for i in np.where(~reg)[0]:
+                S, G = pair_integrals(pts[i], P6, "near", n_near=self.n_near, want_G=True)
+                phi[i] += S @ uT
+                E[i] += uT @ G
+        return phi, E
 
     def integrate(self, u=None):
         """int sigma_h dS (the total charge) for vertex values u, or the area if

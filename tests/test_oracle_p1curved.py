@@ -167,3 +167,44 @@ def test_quadrature_parameters_do_not_change_the_solution(C):
     u1 = C.CurvedProblem(nodes, tri6, nv, eta=4.0, g=8, n=24, n_near=(16, 64)).solve_conductor()
     u2 = C.CurvedProblem(nodes, tri6, nv, eta=2.0, g=12, n=32, n_near=(20, 80)).solve_conductor()
     assert np.abs(u1 - u2).max() < 1e-11
+
+
+def test_flat_field_reduction_to_closed_form(C, oracle_mod):
+    """sum_k of the basis functions' fields G_k = the closed-form field of a
+    constant density (Graglia / solid angle), off the surface: regular and
+    near-singular points, down to 1e-6 R from the triangle."""
+    worst = 0.0
+    for a, b, c in _shaped_triangles(6, 21):
+        P6 = _flat6(a, b, c)
+        cc, R = C.circumcircle(a, b, c)
+        n = np.cross(b - a, c - a)
+        n /= np.linalg.norm(n)
+        ctr = (a + b + c) / 3.0
+        for x, kind in [(cc + 2.0001 * R * n, "regular"), (cc + 5.0 * R * np.array([0.6, 0.0, 0.8]), "regular"),
+                        (ctr + 0.1 * R * n, "near"), (ctr - 1e-6 * R * n, "near"),
+                        (0.5 * (a + b) + 0.01 * R * n, "near"), (a + 0.2 * (a - ctr), "near"),
+                        (b - 1e-4 * R * n, "near")]:
+            _, G = oracle_mod.tri_exact(x, a, b, c)
+            _, Gk = C.pair_integrals(x, P6, kind, want_G=True)
+            worst = max(worst, np.abs(Gk.sum(axis=0) - G).max() / np.abs(G).max())
+    assert worst < 1e-10, worst
+
+
+@pytest.mark.slow
+def test_sphere_field_fourth_order(C):
+    """The conductor sphere's field at 50 points inside (phi = 1, E = 0) and 50
+    outside (phi = 1/r, E = x/r^3) converges at O(h^4) or better."""
+    pts = mg.sphere_eval_points(1, 50, 50)
+    r = np.linalg.norm(pts, axis=1)
+    inside = r < 1.0
+    phi_t = np.where(inside, 1.0, 1.0 / r)
+    E_t = np.where(inside[:, None], 0.0, pts / r[:, None] ** 3)
+    errs = []
+    for level in (1, 2):
+        nodes, tri6, nv = mg.quadratic_sphere(level)
+        P = C.CurvedProblem(nodes, tri6, nv)
+        phi, E = P.field(P.solve_conductor(), pts)
+        errs.append([np.abs(phi - phi_t).max(), np.abs(E - E_t).max()])
+    errs = np.array(errs)
+    assert np.all(errs[1] < [5e-5, 1e-4]), errs
+    assert np.all(errs[0] / errs[1] > 10.0), errs
