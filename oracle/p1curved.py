@@ -25,7 +25,9 @@ What it computes (paper sections / equations):
   collocation point's corner; near-singular pairs after splitting the triangle at
   its point closest to the collocation point, each part collapsed at that point;
 * conductor rows (Eq. Final1): sum_j v_ij u_j = V0, solved by LU (numpy/LAPACK);
-* phi and E of sigma_h at points off the surface (field formula, end of Sec. 2).
+* phi and E of sigma_h at points off the surface (field formula, end of Sec. 2);
+* dielectric rows (Eq. Final3) with K'sigma at a vertex taken as the mean of the
+  two one-sided limits of the normal field (the jump relations of Eq. ADL).
 
 The quadrature orders are not stated in the paper; the defaults here (eta = 2 with
 a 12x12 regular rule, 24x24 singular, near-singular 16 points per radial piece and
@@ -277,6 +279,103 @@ class CurvedProblem:
                 phi[i] += S @ uT
                 E[i] += uT @ G
         return phi, E
+
+    def vertex_normals(self):
+        """Unit normal at every vertex: the sum of the unit normals that the curved
+        triangles around it have at that corner (their maps' dy/dxi x dy/deta),
+        normalised.  The triangles' corners are counter-clockwise about the normal
+        of the + side."""
+        nrm = np.zeros((self.nv, 3))
+        for T in range(self.N):
+            P6 = self.nodes[self.tri6[T]]
+            _, dxi, deta = shape(CORNERS[:, 0], CORNERS[:, 1])
+            n = np.cross(dxi @ P6, deta @ P6)
+            nrm[self.tri6[T, :3]] += n / np.linalg.norm(n, axis=1, keepdims=True)
+        return nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
+
+    def _regular_rule(self):
+        """Every triangle's regular-rule points Y (N, Q, 3) and weights w J (N, Q),
+        the basis values (Q, 3), circumcentres (N, 3) and radii (N,)."""
+        if not hasattr(self, "_rr"):
+            xi, eta, w = duffy(CORNERS[0], CORNERS[1], CORNERS[2], self.g)
+            Y, WJ, CC, R = [], [], [], []
+            for T in range(self.N):
+                P6 = self.nodes[self.tri6[T]]
+                y, J = surface(P6, xi, eta)
+                Y.append(y)
+                WJ.append(w * J)
+                c, r = circumcircle(P6[0], P6[1], P6[2])
+                CC.append(c)
+                R.append(r)
+            self._rr = (np.array(Y), np.array(WJ), linear(xi, eta), np.array(CC), np.array(R))
+        return self._rr
+
+    def basis_fields(self, x):
+        """(nv, 3): the field at x (off the surface) of every basis function psi_v:
+        the regular pairs of all triangles at once, the near-singular ones one by one."""
+        Y, WJ, lam, CC, R = self._regular_rule()
+        out = np.zeros((self.nv, 3))
+        reg = np.linalg.norm(x - CC, axis=1) > self.eta * R
+        d = x - Y[reg]
+        r = np.linalg.norm(d, axis=2)
+        G = np.einsum("tq,qk,tqc->tkc", WJ[reg] / r ** 3, lam, d) / FOUR_PI
+        np.add.at(out, self.tri6[reg, :3], G)
+        for T in np.where(~reg)[0]:
+            _, G = pair_integrals(x, self.nodes[self.tri6[T]], "near", n_near=self.n_near, want_G=True)
+            out[self.tri6[T, :3]] += G
+        return out
+
+    def kprime_rows(self, rows, delta_rel: float = 1e-3):
+        """(len(rows), nv): (K' psi_v)(x_i) for the vertices i in rows, by the jump
+        relations of Eq. ADL read as Plemelj's formulas: K'sigma = (E+.n + E-.n)/2,
+        the mean of the two one-sided limits of the normal field.  Each limit is the
+        field at x_i +- delta n_i, extrapolated to delta -> 0 from delta and 2 delta
+        (Richardson); delta = delta_rel times the mean length of the edges at x_i."""
+        nrm = self.vertex_normals()
+        X = self.nodes[: self.nv]
+        e = np.concatenate([self.tri6[:, [0, 1]], self.tri6[:, [1, 2]], self.tri6[:, [2, 0]]])
+        L = np.linalg.norm(X[e[:, 0]] - X[e[:, 1]], axis=1)
+        hsum = np.bincount(e[:, 0], L, self.nv) + np.bincount(e[:, 1], L, self.nv)
+        hcnt = np.bincount(e[:, 0], None, self.nv) + np.bincount(e[:, 1], None, self.nv)
+        h = hsum / hcnt
+        out = np.zeros((len(rows), self.nv))
+        for k, i in enumerate(rows):
+            n = nrm[i]
+            d = delta_rel * h[i]
+            f = {}
+            for m in (1, 2):
+                Ep = self.basis_fields(X[i] + m * d * n) @ n
+                Em = self.basis_fields(X[i] - m * d * n) @ n
+                f[m] = 0.5 * (Ep + Em)
+            out[k] = 2.0 * f[1] - f[2]
+        return out
+
+    def solve(self, regions, body, V0_scale: float = 1.0):
+        """u at the vertices for regions (dicts, as for flat meshes) given per
+        triangle by body: conductor rows sum_j v_ij u_j = V0 (Eq. Final1),
+        dielectric rows (eps+ + eps-)/2 u_i + (eps+ - eps-) (K'u)_i = 0
+        (Eq. Final3).  A vertex takes the region of its triangles."""
+        vreg = np.full(self.nv, -1)
+        for T in range(self.N):
+            for v in self.tri6[T, :3]:
+                assert vreg[v] in (-1, body[T]), "a vertex on two regions"
+                vreg[v] = body[T]
+        kinds = [regions[r]["kind"] for r in vreg]
+        A = np.zeros((self.nv, self.nv))
+        b = np.zeros(self.nv)
+        cond = [i for i in range(self.nv) if kinds[i] == "conductor"]
+        diel = [i for i in range(self.nv) if kinds[i] == "dielectric"]
+        assert len(cond) + len(diel) == self.nv, "only conductor and dielectric rows"
+        if cond:
+            A[cond] = self.matrix()[cond]
+            b[cond] = [regions[vreg[i]]["V0"] * V0_scale for i in cond]
+        if diel:
+            K = self.kprime_rows(diel)
+            for k, i in enumerate(diel):
+                ep, em = regions[vreg[i]]["eps_plus"], regions[vreg[i]]["eps_minus"]
+                A[i] = (ep - em) * K[k]
+                A[i, i] += 0.5 * (ep + em)
+        return np.linalg.solve(A, b), vreg
 
     def integrate(self, u=None):
         """int sigma_h dS (the total charge) for vertex values u, or the area if

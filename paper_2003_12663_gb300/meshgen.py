@@ -322,6 +322,26 @@ def quadratic_sphere(level: int, radius: float = 1.0):
     return nodes, tri6, len(X)
 
 
+def quadratic_bodies(parts):
+    """Merge six-node meshes [(nodes, tri6, nv), ...] into one whose first nodes are
+    all the triangle corners (body by body), then all the edge nodes.  Returns
+    (nodes, tri6, nv, body) with body[T] the index of the part triangle T came from."""
+    corners = sum(nv for _, _, nv in parts)
+    c_off, e_off = 0, corners
+    N, T6, B, C, E = [], [], [], [], []
+    for k, (nodes, tri6, nv) in enumerate(parts):
+        ne = len(nodes) - nv
+        remap = np.concatenate([c_off + np.arange(nv), e_off + np.arange(ne)])
+        C.append(nodes[:nv])
+        E.append(nodes[nv:])
+        T6.append(remap[tri6])
+        B.append(np.full(len(tri6), k, np.int32))
+        c_off += nv
+        e_off += ne
+    nodes = np.concatenate(C + E)
+    return nodes, np.concatenate(T6).astype(np.int32), corners, np.concatenate(B)
+
+
 def jitter(X: np.ndarray, tri: np.ndarray, frac: float, seed: int, movable=None) -> np.ndarray:
     """Move each vertex by U(-frac, frac) * (mean length of its edges), per coordinate."""
     rng = np.random.default_rng(seed)

@@ -208,3 +208,42 @@ def test_sphere_field_fourth_order(C):
     errs = np.array(errs)
     assert np.all(errs[1] < [5e-5, 1e-4]), errs
     assert np.all(errs[0] / errs[1] > 10.0), errs
+
+
+@pytest.mark.slow
+def test_conductor_inside_dielectric_sphere_curved(C, oracle_mod):
+    """Eqs. Final1 + Final3 on concentric spheres: a conductor (a = 1, V0 = 1)
+    inside a dielectric ball (b = 2, eps_r = 4 inside, 1 outside).  Gauss gives the
+    charges Q/eps on the conductor and Q (1 - 1/eps) on the interface, with
+    Q = 4 pi V0 / (1/(eps a) + (1 - 1/eps)/b).  With K' as the mean of the one-sided
+    normal fields, curved P1 converges at about third order (flat P0, whose K'
+    misses the curvature of its own panel, at first order) and at level 2 is far
+    more accurate than flat P0 on the same vertices."""
+    a, b, eps, V0 = 1.0, 2.0, 4.0, 1.0
+    Q = FOUR_PI * V0 / (1.0 / (eps * a) + (1.0 - 1.0 / eps) / b)
+    want = np.array([Q / eps, Q * (1.0 - 1.0 / eps)])
+    regions = [{"kind": "conductor", "V0": V0}, {"kind": "dielectric", "eps_plus": 1.0, "eps_minus": eps}]
+    errs = []
+    for level in (1, 2):
+        nodes, tri6, nv, body = mg.quadratic_bodies([mg.quadratic_sphere(level, a), mg.quadratic_sphere(level, b)])
+        P = C.CurvedProblem(nodes, tri6, nv)
+        u, vreg = P.solve(regions, body)
+        xi, eta, w = C.duffy(C.CORNERS[0], C.CORNERS[1], C.CORNERS[2], 12)
+        lam = C.linear(xi, eta)
+        q = np.zeros(2)
+        for T in range(P.N):
+            _, J = C.surface(nodes[tri6[T]], xi, eta)
+            q[body[T]] += np.sum(w * J * (lam @ u[tri6[T, :3]]))
+        errs.append(np.abs(q - want) / want)
+    errs = np.array(errs)
+    assert np.all(errs[1] < 6e-3), errs
+    assert np.all(errs[0] / errs[1] > 5.0), errs
+    # flat P0 on the same two icospheres (centroid collocation)
+    X1, T1 = mg.icosphere(2, a)
+    X2, T2 = mg.icosphere(2, b)
+    flat = mg.Mesh(np.concatenate([X1, X2]), np.concatenate([T1, T2 + len(X1)]).astype(np.int32),
+                   np.concatenate([np.zeros(len(T1), np.int32), np.ones(len(T2), np.int32)]), regions)
+    Pf = oracle_mod.Problem(flat, eta=4.0, g=3)
+    uf = Pf.solve()
+    qf = np.array([np.sum((uf[: Pf.N] * Pf.area)[flat.region == k]) for k in (0, 1)])
+    assert np.all(errs[1] < np.abs(qf - want) / want / 5.0), (errs[1], np.abs(qf - want) / want)
