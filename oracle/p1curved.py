@@ -27,7 +27,8 @@ What it computes (paper sections / equations):
 * conductor rows (Eq. Final1): sum_j v_ij u_j = V0, solved by LU (numpy/LAPACK);
 * phi and E of sigma_h at points off the surface (field formula, end of Sec. 2);
 * dielectric rows (Eq. Final3) with K'sigma at a vertex taken as the mean of the
-  two one-sided limits of the normal field (the jump relations of Eq. ADL).
+  two one-sided limits of the normal field (the jump relations of Eq. ADL);
+* floating conductors (Eqs. Final2, Final4), the neutrality row by Gauss's law.
 
 The quadrature orders are not stated in the paper; the defaults here (eta = 2 with
 a 12x12 regular rule, 24x24 singular, near-singular 16 points per radial piece and
@@ -351,24 +352,46 @@ class CurvedProblem:
         return out
 
     def solve(self, regions, body, V0_scale: float = 1.0):
-        """u at the vertices for regions (dicts, as for flat meshes) given per
-        triangle by body: conductor rows sum_j v_ij u_j = V0 (Eq. Final1),
-        dielectric rows (eps+ + eps-)/2 u_i + (eps+ - eps-) (K'u)_i = 0
-        (Eq. Final3).  A vertex takes the region of its triangles."""
+        """Unknowns (u at the vertices, then V_f of each floating body) for regions
+        (dicts, as for flat meshes) given per triangle by body:
+          conductor rows  sum_j v_ij u_j = V0                      (Eq. Final1)
+          floating rows   sum_j v_ij u_j - V_f = 0                  (Eq. Final2)
+          dielectric rows (eps+ + eps-)/2 u_i + (eps+ - eps-) (K'u)_i = 0  (Eq. Final3)
+          neutrality      int_{body f} sigma_h dS = 0               (Eq. Final4)
+        The neutrality row uses Gauss's law on a closed conductor (no field inside):
+        int eps+ (sigma/2 + K'sigma) dS = eps+ int E+.n dS = eps+ int sigma dS.
+        A vertex takes the region of its triangles.  Returns (x, vreg)."""
         vreg = np.full(self.nv, -1)
         for T in range(self.N):
             for v in self.tri6[T, :3]:
                 assert vreg[v] in (-1, body[T]), "a vertex on two regions"
                 vreg[v] = body[T]
         kinds = [regions[r]["kind"] for r in vreg]
-        A = np.zeros((self.nv, self.nv))
-        b = np.zeros(self.nv)
+        fids = sorted({r["floating_id"] for r in regions if r["kind"] == "floating"})
+        F = len(fids)
+        n = self.nv + F
+        A = np.zeros((n, n))
+        b = np.zeros(n)
         cond = [i for i in range(self.nv) if kinds[i] == "conductor"]
+        flo = [i for i in range(self.nv) if kinds[i] == "floating"]
         diel = [i for i in range(self.nv) if kinds[i] == "dielectric"]
-        assert len(cond) + len(diel) == self.nv, "only conductor and dielectric rows"
-        if cond:
-            A[cond] = self.matrix()[cond]
+        assert len(cond) + len(flo) + len(diel) == self.nv, "conductor, floating and dielectric rows only"
+        if cond or flo:
+            V = self.matrix()
+            A[cond, : self.nv] = V[cond]
             b[cond] = [regions[vreg[i]]["V0"] * V0_scale for i in cond]
+            for i in flo:
+                A[i, : self.nv] = V[i]
+                A[i, self.nv + fids.index(regions[vreg[i]]["floating_id"])] = -1.0
+        if flo:
+            xi, eta, w = duffy(CORNERS[0], CORNERS[1], CORNERS[2], self.g)
+            lam = linear(xi, eta)
+            for T in range(self.N):
+                R = regions[body[T]]
+                if R["kind"] != "floating":
+                    continue
+                _, J = surface(self.nodes[self.tri6[T]], xi, eta)
+                A[self.nv + fids.index(R["floating_id"]), self.tri6[T, :3]] += (w * J) @ lam
         if diel:
             K = self.kprime_rows(diel)
             for k, i in enumerate(diel):

@@ -247,3 +247,33 @@ def test_conductor_inside_dielectric_sphere_curved(C, oracle_mod):
     uf = Pf.solve()
     qf = np.array([np.sum((uf[: Pf.N] * Pf.area)[flat.region == k]) for k in (0, 1)])
     assert np.all(errs[1] < np.abs(qf - want) / want / 5.0), (errs[1], np.abs(qf - want) / want)
+
+
+@pytest.mark.slow
+def test_floating_sphere_next_to_conductor_curved(C):
+    """Eqs. Final1, Final2, Final4 on curved P1: a conductor sphere (a = 1 at V0 = 1)
+    and a neutral floating sphere (a = 0.5, centres 2.5 apart).  The floating
+    potential and the conductor's charge approach the method-of-images series at
+    about fourth order; the floating sphere's net charge is zero to rounding."""
+    from test_oracle_solve import two_sphere_images
+    a1, a2, d, V1 = 1.0, 0.5, 2.5, 1.0
+    V2, Q1 = two_sphere_images(a1, a2, d, V1)
+    regions = [{"kind": "conductor", "V0": V1}, {"kind": "floating", "floating_id": 0, "eps_plus": 1.0}]
+    errs = []
+    for level in (1, 2):
+        n2, t2, nv2 = mg.quadratic_sphere(level, a2)
+        nodes, tri6, nv, body = mg.quadratic_bodies([mg.quadratic_sphere(level, a1),
+                                                     (n2 + np.array([d, 0.0, 0.0]), t2, nv2)])
+        P = C.CurvedProblem(nodes, tri6, nv)
+        x, vreg = P.solve(regions, body)
+        xi, eta, w = C.duffy(C.CORNERS[0], C.CORNERS[1], C.CORNERS[2], 12)
+        lam = C.linear(xi, eta)
+        q = np.zeros(2)
+        for T in range(P.N):
+            _, J = C.surface(nodes[tri6[T]], xi, eta)
+            q[body[T]] += np.sum(w * J * (lam @ x[tri6[T, :3]]))
+        assert abs(q[1]) < 1e-12 * abs(q[0])
+        errs.append([abs(x[nv] - V2) / V2, abs(q[0] - Q1) / Q1])
+    errs = np.array(errs)
+    assert np.all(errs[1] < 1e-4), errs
+    assert np.all(errs[0] / errs[1] > 8.0), errs
