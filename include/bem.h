@@ -304,7 +304,8 @@ int bem_matvec_transpose(bem_ctx* ctx, int32_t precision, const double* x_dev, d
  * Outputs (device, any may be NULL): K_dev double [L]; gX_dev double [nv][3];
  * gV0_dev double [nregions] (dJ/dV0 of every conductor region, 0 elsewhere);
  * geps_dev double [nregions][2] (dJ/d eps_plus, dJ/d eps_minus; eps_plus of a
- * floating region enters its neutrality row).  Allocates temporary device memory
+ * floating region enters its neutrality row, and both permittivities of a sheet
+ * enter its row of Eq. sheets).  Allocates temporary device memory
  * (the tape: ~88 bytes per step and line) and synchronises.  BEM_ERR_ARG if a line
  * ends on another electrode or in a singular field (status 2 or -1).  far_order 2..4.
  */
