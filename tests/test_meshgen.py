@@ -70,3 +70,21 @@ def test_bushing_and_sheet_meshes():
     assert m.regions[-1]["V0"] == 0.0
     s = mg.sphere_in_sheet_mesh(2)
     assert s.n_floating == 1 and s.regions[1]["eps_minus"] == 4.0
+
+
+def test_quadratic_meshes():
+    """Six-node triangles: corner nodes first (the P1 unknowns), edge nodes on the
+    sphere, every edge node shared by the two triangles of its edge; merging
+    bodies keeps all corners ahead of all edge nodes."""
+    nodes, tri6, nv = mg.quadratic_sphere(1, 2.0)
+    assert nv == 42 and len(nodes) == 42 + 120 and tri6.shape == (80, 6)
+    assert np.all(tri6[:, :3] < nv) and np.all(tri6[:, 3:] >= nv)
+    assert np.allclose(np.linalg.norm(nodes, axis=1), 2.0)
+    _, cnt = np.unique(tri6[:, 3:], return_counts=True)
+    assert np.all(cnt == 2)
+    n2, t2, nv2 = mg.quadratic_sphere(0, 0.5)
+    m, t, nvm, body = mg.quadratic_bodies([(nodes, tri6, nv), (n2 + 3.0, t2, nv2)])
+    assert nvm == nv + nv2 and len(m) == len(nodes) + len(n2)
+    assert np.all(t[:, :3] < nvm) and np.all(t[:, 3:] >= nvm)
+    assert np.allclose(m[t[body == 1]], (n2 + 3.0)[t2])
+    assert np.allclose(m[t[body == 0]], nodes[tri6])
