@@ -155,3 +155,20 @@ def test_linearity_in_V0(oracle_mod):
     u1 = P.solve(A=A)
     for s in (0.5, -1.0, 2.0):
         assert np.allclose(P.solve(V0_scale=s, A=A), s * u1, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("name", ["device", "sheet", "bushing"])
+def test_matrix_free_product_equals_assembled(name):
+    """The oracle's matrix-free product (field sums at the centroids, then the row
+    equations) equals the assembled matrix times x, for every row kind: conductor,
+    floating and dielectric rows, neutrality rows of closed bodies and of sheets."""
+    from oracle import oracle as O
+    mesh = {"device": lambda: mg.device_mesh(scale=0.3),
+            "sheet": lambda: mg.sphere_in_sheet_mesh(2),
+            "bushing": lambda: mg.bushing_mesh(0.2)}[name]()
+    P = O.Problem(mesh, eta=4.0, g=3)
+    A = P.assemble()
+    x = np.random.default_rng(21).normal(size=A.shape[0])
+    y = P.matvec(x)
+    ref = A @ x
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
