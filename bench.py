@@ -1,16 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the panel-interaction hot path on one GB300 (or N replicas).
 
-Workload (one "step"): the multi-domain device -- conductor sphere R=1 at V0=1,
-floating torus (R=2, r=0.3) with its charge-neutrality row, dielectric
-cylinder eps_r=4 -- meshed with about 20k flat triangles (seeded), then
+Workload (one "step"): the large matrix-free run -- the multi-domain device
+(conductor sphere R=1 at V0=1, floating torus (R=2, r=0.3) with its
+charge-neutrality row, dielectric cylinder eps_r=4) meshed with about 200k flat
+triangles (seeded), then
   1. the matrix-free solve: GMRES on the mixed-precision matvec (FP32 regular
-     pairs, FP64 near pairs and Arnoldi) inside an FP64 iterative refinement to
-     a relative residual of 1e-8,
+     pairs, FP64 near pairs and Arnoldi) inside an FP64-accurate iterative
+     refinement to a relative residual of 1e-8,
   2. the surface field E+ at every centroid,
-  3. phi and E at 1e5 points uniform in [-4,4]^3 outside the conductors.
+  3. phi and E at 1e6 points uniform in [-4,4]^3 outside the conductors.
 Metric: Ginteractions/s = (target, triangle) pairs evaluated by all kernel
-launches of the step / step time (whole job over all ranks).
+launches of the step / step time (whole job over all ranks).  The same step on
+the 20k device, and the plain FP64 form of both, are reported beside it.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -37,6 +39,7 @@ FLOPS_PER_PAIR_OP = 18        # phi+E per (target, quadrature node): 3 sub, 5 fo
 PHI_FLOPS_PER_PAIR_OP = 10    # phi alone: 3 sub, 5 for r^2, w/r, phi+=
 FP32_LANES_PER_SM = 128
 TOL = 1e-8
+C5_SCALE = (200000 / 20068.0) ** 0.5   # mesh scale of the ~200k-triangle device
 
 
 def parse():
@@ -45,8 +48,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--scale", type=float, default=1.0, help="mesh scale (1.0: ~20k triangles)")
-    ap.add_argument("--points", type=int, default=100000)
+    ap.add_argument("--scale", type=float, default=None,
+                    help="mesh scale (default: ~200k triangles, trace mode ~20k; 1.0: ~20k)")
+    ap.add_argument("--points", type=int, default=1000000)
+    ap.add_argument("--no-c2", action="store_true", help="skip the 20k-device comparison")
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -60,6 +65,10 @@ def parse():
     ap.add_argument("--report-configs", default="c1,c2,c3,bushing,c5", help="report mode: configurations")
     ap.add_argument("--c5-lines", type=int, default=64, help="report mode: field lines traced on c5")
     ap.add_argument("--lines", type=int, default=512, help="trace mode: field lines")
+    ap.add_argument("--seed-radius", type=float, default=1.05,
+                    help="trace mode: radius of the sphere the Fibonacci seeds lie on")
+    ap.add_argument("--batch-points", type=int, default=10000,
+                    help="batch mode: field points per mesh for bem_batch_eval_field")
     ap.add_argument("--max-steps", type=int, default=200000, help="trace mode: RK4 step limit per line")
     ap.add_argument("--instances", type=int, default=64, help="batch mode: meshes in the family")
     ap.add_argument("--nrhs", type=int, default=4, help="batch mode: right-hand sides per mesh")
@@ -85,20 +94,32 @@ def run_matvec(args):
     ctx.close()
 
 
-def workload(args):
+def workload(args, scale=None, points=None):
     from paper_2003_12663_gb300 import meshgen as mg
-    mesh = mg.device_mesh(scale=args.scale, seed=2)
-    pts = mg.device_box_points(args.points, seed=5)
+    scale = scale if scale is not None else (args.scale if args.scale is not None else C5_SCALE)
+    mesh = mg.device_mesh(scale=scale, seed=2)
+    pts = mg.device_box_points(points if points is not None else args.points, seed=5)
     return mesh, pts
 
 
-def config_of(args, mesh, extra=None):
-    cfg = {"workload": "multi-domain device (conductor sphere, floating torus, dielectric cylinder)",
+def workload_name(mesh):
+    big = mesh.np_ > 100000
+    return (("large matrix-free run: " if big else "") +
+            f"multi-domain device (conductor sphere, floating torus, dielectric cylinder) at "
+            f"{mesh.np_} triangles; mixed solve to {TOL}, surface field, field at box points")
+
+
+def config_of(args, mesh, n_points, extra=None):
+    cfg = {"workload": workload_name(mesh),
            "triangles": int(mesh.np_), "unknowns": int(mesh.n_unknowns),
            "counts_sphere_torus_cylinder": list(mesh.info["counts"]),
-           "eval_points": int(args.points), "gmres_tol": TOL, "solver": "GMRES(100)+FP64 refinement",
+           "eval_points": int(n_points), "gmres_tol": TOL, "solver": "GMRES(100)+FP64-accurate refinement",
            "far_rule": "3x3 Duffy/Gauss, eta=4", "l2": "flushed (256 MB write) before every step",
            "parallelism": f"replicas x{args.gpus}"}
+    if mesh.np_ > 100000:
+        cfg["reading"] = ("the large configuration's device is the three-body device of the 20k "
+                          "configuration refined to ~200k triangles; its field lines are reported by "
+                          "--mode report, not in this step")
     if extra:
         cfg.update(extra)
     return cfg
@@ -181,8 +202,8 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline inputs
-def fp32_peak_tflops(num_sms):
-    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flop (FFMA) x max SM clock."""
+def fp32_peak_derived(num_sms):
+    """FP32 CUDA-core peak from unit counts: SMs x 128 lanes x 2 flop (FFMA) x max SM clock."""
     mhz = None
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -195,6 +216,20 @@ def fp32_peak_tflops(num_sms):
     return num_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, mhz
 
 
+def fp32_peak(bem, num_sms):
+    """(peak TFLOP/s, basis): the FP32 rate measured by bem_measure_peaks (paired and
+    scalar FP32 multiply-add chains at full occupancy), else the derived figure."""
+    derived, mhz = fp32_peak_derived(num_sms)
+    try:
+        m = bem.measure_peaks()
+    except Exception as e:  # the measurement is reported, never silently replaced
+        return derived, f"derived ({num_sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz); measurement failed: {e}", None
+    basis = (f"measured: bem_measure_peaks, FP32 multiply-add chains at full occupancy "
+             f"(paired {m['fp32_tflops']:.1f}, scalar {m['fp32_scalar_tflops']:.1f} TFLOP/s); "
+             f"derived {derived:.1f} ({num_sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz)")
+    return m["fp32_tflops"], basis, m
+
+
 def far_kernel_hash():
     """sha256[:16] of the packed FP32 kernel's source (from its section marker to
     the next kernel): the committed ncu counters stay valid while it is unchanged."""
@@ -204,10 +239,12 @@ def far_kernel_hash():
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def committed_traffic():
-    """DRAM bytes per launch of the FP32 regular-pair kernel from the committed ncu
-    summary, if it was taken on the current far.cu (else None)."""
-    p = os.path.join(ROOT, "profiles", "far32_device20k.md")
+def committed_traffic(profile):
+    """DRAM bytes per launch of the FP32 regular-pair kernel, copied from the committed
+    ncu summary profiles/<profile> when it was captured on the current kernel source
+    (its 'k_far32p source sha256[:16]' line); else None.  This is a stored capture,
+    not a measurement of this run, and the bench line says so."""
+    p = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(p):
         return None
     vals = {}
@@ -224,30 +261,68 @@ def committed_traffic():
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_oracle_rate(mesh, seconds, seed=0):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_oracle_rate(mesh, seconds, seed=0, threads=0):
     """Oracle throughput (pairs/s) on a bounded sample: the pair integrals of a
     seeded sample of collocation rows against all triangles (classification,
-    Duffy/Gauss rule, closed form), OpenMP on all host cores."""
+    Duffy/Gauss rule, closed form), OpenMP on `threads` host cores (0: all)."""
     from oracle import oracle as O
-    P = O.Problem(mesh, eta=4.0, g=3)
-    rng = np.random.default_rng(seed)
-    rows = 16
-    t = 0.0
-    while True:
-        idx = np.sort(rng.choice(P.N, size=min(rows, P.N), replace=False))
+    before = O.set_threads(threads) if threads > 0 else None
+    try:
+        P = O.Problem(mesh, eta=4.0, g=3)
+        rng = np.random.default_rng(seed)
+        rows = 4
+        while True:
+            idx = np.sort(rng.choice(P.N, size=min(rows, P.N), replace=False))
+            t0 = time.perf_counter()
+            P.pair_block(P.centroids[idx], idx, want_G=True)
+            t = time.perf_counter() - t0
+            if t > seconds / 4 or rows >= P.N:
+                break
+            rows *= 2
+        # the timed sample
+        idx = np.sort(rng.choice(P.N, size=min(rows * 2, P.N), replace=False))
         t0 = time.perf_counter()
         P.pair_block(P.centroids[idx], idx)
         t = time.perf_counter() - t0
-        if t > seconds / 4 or rows >= P.N:
-            break
-        rows *= 2
-    # the timed sample
-    idx = np.sort(rng.choice(P.N, size=min(rows * 2, P.N), replace=False))
-    t0 = time.perf_counter()
-    P.pair_block(P.centroids[idx], idx)
-    t = time.perf_counter() - t0
-    pairs = len(idx) * P.N
-    return pairs / t, len(idx), t
+    finally:
+        if before is not None:
+            O.set_threads(before)
+    return len(idx) * P.N / t, len(idx), t
+
+
+def events_ms(fn, stream, n, flush=None):
+    """CUDA-event times (ms) of n calls of fn on stream, L2 flushed before each."""
+    import torch
+    out = []
+    for _ in range(n):
+        if flush is not None:
+            flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -265,6 +340,8 @@ def run_ours(args):
 
     mesh, pts = workload(args)
     dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    peak, peak_basis, peaks = fp32_peak(bem, props.multi_processor_count)
     ctx = bem.Context(mesh, timing=1, far32_variant=args.far32_variant)
     Q = ctx.params.far_order ** 2
     pts_d = torch.tensor(pts, device=dev)
@@ -305,8 +382,6 @@ def run_ours(args):
     launches = cnt["kernel_launches"]
 
     # roofline of the dominant kernel: the FP32 regular-pair kernel
-    props = torch.cuda.get_device_properties(dev)
-    peak, mhz = fp32_peak_tflops(props.multi_processor_count)
     far_pairs = cnt["pairs"][1] - cnt["near_pairs"][1]
     # tiles of conductor rows sum phi alone: 10 of the 18 flops of a pair-op
     phi_far = cnt["phi_pairs"][1] * (far_pairs / max(cnt["pairs"][1], 1))
@@ -314,104 +389,192 @@ def run_ours(args):
     far_ms = cnt["far_ms"][1]
     achieved = flops / (far_ms * 1e-3) / 1e12 if far_ms > 0 else None
     n_launch = max(cnt["far_launches"][1], 1)
-    traffic = committed_traffic()
+    profile = "far32_device200k.md" if mesh.np_ > 100000 else "far32_device20k.md"
+    traffic = committed_traffic(profile)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_source": (f"copied from the committed ncu capture profiles/{profile} "
+                                   f"(same k_far32p source hash {far_kernel_hash()}), not measured in this run"
+                                   if traffic is not None else
+                                   f"null: no ncu capture of the current k_far32p source in profiles/{profile}"),
                 "kernel": ("k_far32 (scalar)" if cnt["far32_variant"] == 1 else
                            f"k_far32p (packed f32x2, {cnt['far32_variant']} target pairs/thread)")
                           + ": FP32 regular pairs, phi+E",
-                "peak_basis": f"derived FP32 peak: {props.multi_processor_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz",
+                "peak_basis": peak_basis,
+                "flops_basis": f"{Q} nodes x ({FLOPS_PER_PAIR_OP} x far pairs - 8 x far pairs of phi-only tiles)",
                 "flops_per_launch": flops / n_launch, "avg_launch_ms": far_ms / n_launch,
+                "launches_timed": cnt["far_launches"][1],
                 "phi_only_pair_share": cnt["phi_pairs"][1] / max(cnt["pairs"][1], 1),
+                "fast_chunk_share": (cnt["fast_chunks32p"] / cnt["chunks32p"]) if cnt["chunks32p"] else None,
                 "fp64_far_ms_per_step": cnt["far_ms"][0] / args.steps,
                 "df_residual_far_ms_per_step": cnt["far_ms"][2] / args.steps,
                 "fp32_far_ms_per_step": far_ms / args.steps}
+    if peaks:
+        roofline["fp64_peak_tflops_measured"] = peaks["fp64_tflops"]
 
-    # accuracy of the step's solve (FP64 residual from the solver)
     rel = out["rel"][0]
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "f32 regular pairs + f64",
               "data": "synthetic (seeded meshes and points)",
-              "config": config_of(args, mesh, {"gmres_iters_per_step": cnt["gmres_iters"] / args.steps,
-                                               "fp64_relres": rel,
-                                               "pairs_per_step": pairs_step}),
+              "config": config_of(args, mesh, len(pts),
+                                  {"gmres_iters_per_step": cnt["gmres_iters"] / args.steps,
+                                   "products_per_step": {"mixed": cnt["matvecs"][1] / args.steps,
+                                                         "double_fp32_residual": cnt["matvecs"][2] / args.steps},
+                                   "fp64_relres": rel, "pairs_per_step": pairs_step}),
               "roofline": roofline, "gpu_launches": launches}
     if clk:
         result["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
 
-    # the plain FP64 form of the same step, once (context for the mixed-precision claim)
     if not args.no_fp64_form and rank == 0:
-        ctx.reset_counters()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        u64, it64, rel64 = ctx.solve(bem.FP64, tol=TOL)
-        ctx.surface_field(u64[0], bem.FP64)
-        ctx.eval_field(u64[0], pts_d, bem.FP64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        c64 = ctx.counters()
-        ms64 = e0.elapsed_time(e1)
-        du = (torch.linalg.norm(out["u"][0] - u64[0]) / torch.linalg.norm(u64[0])).item()
-        dE = ((out["E"] - ctx.eval_field(u64[0], pts_d, bem.FP64)[1]).abs().max()
-              / out["E"].abs().max()).item()
-        result["fp64_form"] = {"ms_per_step": ms64, "gmres_iters": it64, "relres": rel64[0],
-                               "value": sum(c64["pairs"]) / (ms64 * 1e-3) / 1e9,
-                               "mixed_speedup": ms64 / ms,
-                               "sigma_rel_l2_mixed_vs_fp64": du, "E_rel_mixed_vs_fp64": dE}
+        result["fp64_form"] = fp64_form(args, bem, ctx, mesh, pts_d, out, cnt, ms, stream, flush)
+    if not args.no_c2 and rank == 0 and mesh.np_ > 100000:
+        result["c2"] = c2_block(args, bem, stream, flush)
 
-    # end to end through the C ABI with host buffers
     if not args.no_e2e:
-        X_h = torch.tensor(pts).pin_memory()
-        phi_h = torch.empty(args.points, dtype=torch.float64).pin_memory()
-        E_h = torch.empty((args.points, 3), dtype=torch.float64).pin_memory()
-        Es_h = torch.empty((mesh.np_, 3), dtype=torch.float64).pin_memory()
-        u_h = torch.empty(mesh.n_unknowns, dtype=torch.float64).pin_memory()
-
-        def e2e_step():
-            c2 = bem.Context(mesh)           # host mesh -> device inside bem_create
-            p_d = X_h.to(dev, non_blocking=True)
-            u, it, rel = c2.solve(bem.MIXED, tol=TOL)
-            Es = c2.surface_field(u[0], bem.MIXED)
-            phi, E = c2.eval_field(u[0], p_d, bem.MIXED)
-            u_h.copy_(u[0], non_blocking=True)
-            Es_h.copy_(Es, non_blocking=True)
-            phi_h.copy_(phi, non_blocking=True)
-            E_h.copy_(E, non_blocking=True)
-            torch.cuda.synchronize()
-            c2.close()
-
-        e2e_step()
-        n_e2e = max(2, min(args.steps, 3))
-        dist_barrier(dist)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            flush.add_(1.0)
-            e2e_step()
-        torch.cuda.synchronize()
-        dist_barrier(dist)
-        e2e_ms = dist_max(dist, (time.perf_counter() - t0) * 1e3 / n_e2e, dev)
-        h2d = mesh.X.size * 8 + mesh.tri.size * 4 + mesh.region.size * 4 + pts.size * 8
-        d2h = mesh.n_unknowns * 8 + mesh.np_ * 24 + args.points * 32
-        result["e2e"] = {"value": world * pairs_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
-                         "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d),
-                         "d2h_bytes_per_step": int(d2h),
-                         "includes": "bem_create from host mesh, H2D points, solve, surface field, eval, D2H"}
+        result["e2e"] = e2e_block(args, bem, mesh, pts, dev, flush, dist, world, pairs_step)
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         rate, rows, secs = cpu_oracle_rate(mesh, args.cpu_seconds)
+        rate1, rows1, secs1 = cpu_oracle_rate(mesh, args.cpu_seconds / 2, seed=1, threads=1)
         result["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": os.cpu_count(),
-                                  "kind": "oracle",
+                                  "kind": "oracle", "cpu_model": cpu_model(),
                                   "sample": f"oracle pair integrals (classification, Duffy/Gauss, closed form; "
                                             f"FP64, OpenMP) of {rows} seeded collocation rows x {mesh.np_} "
-                                            f"triangles, {secs:.1f} s"}
+                                            f"triangles, {secs:.1f} s",
+                                  "one_thread": {"value": rate1 / 1e9, "unit": UNIT, "cores": 1,
+                                                 "sample": f"{rows1} rows x {mesh.np_} triangles, {secs1:.1f} s"}}
     ctx.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
+
+def fp64_form(args, bem, ctx, mesh, pts_d, out, cnt, ms_mixed, stream, flush):
+    """The plain FP64 GPU form of the same step.  On the ~200k device it would take
+    about half an hour, so it is extrapolated from measured parts: one FP64 product
+    (timed), times the products of the mixed step (its GMRES products and refinement
+    residuals) plus one for the surface field, plus the FP64 field at a sample of the
+    points scaled to all of them.  Smaller meshes run it in full (median of 5)."""
+    import torch
+    M = pts_d.shape[0]
+    if mesh.np_ <= 100000:
+        res = {}
+
+        def step64():
+            u64, it64, rel64 = ctx.solve(bem.FP64, tol=TOL)
+            ctx.surface_field(u64[0], bem.FP64)
+            phi, E = ctx.eval_field(u64[0], pts_d, bem.FP64)
+            res.update(u=u64, it=it64, rel=rel64, E=E)
+
+        t = events_ms(step64, stream, 5, flush)
+        ms64 = float(np.median(t))
+        du = (torch.linalg.norm(out["u"][0] - res["u"][0]) / torch.linalg.norm(res["u"][0])).item()
+        dE = ((out["E"] - res["E"]).abs().max() / res["E"].abs().max()).item()
+        return {"ms_per_step": ms64, "runs_ms": t, "statistic": "median of 5", "gmres_iters": res["it"],
+                "relres": res["rel"][0], "mixed_speedup": ms64 / ms_mixed,
+                "sigma_rel_l2_mixed_vs_fp64": du, "E_rel_mixed_vs_fp64": dE}
+    u = out["u"][0]
+    t_mv = events_ms(lambda: ctx.matvec(u, bem.FP64), stream, 2, flush)
+    t_mv64 = float(np.median(t_mv))
+    products = (cnt["matvecs"][1] + cnt["matvecs"][2]) / args.steps
+    n_sub = min(M, 20000)
+    sub = pts_d[:n_sub]
+    holder = {}
+    t_ev = events_ms(lambda: holder.update(r=ctx.eval_field(u, sub, bem.FP64)), stream, 1, flush)[0]
+    _, E64 = holder["r"]
+    dE = ((out["E"][:n_sub] - E64).abs().max() / E64.abs().max()).item()
+    ms64 = (products + 1) * t_mv64 + t_ev * (M / n_sub)
+    return {"ms_per_step": ms64, "extrapolated": True,
+            "basis": f"(products of the mixed step {products:.0f} + 1 surface field) x one FP64 product "
+                     f"{t_mv64:.0f} ms (timed) + FP64 field at {n_sub} of the {M} points "
+                     f"{t_ev:.0f} ms (timed) x {M / n_sub:.0f}",
+            "fp64_product_ms": t_mv, "fp64_eval_sample_ms": t_ev, "mixed_speedup": ms64 / ms_mixed,
+            "E_rel_mixed_vs_fp64_on_sample": dE}
+
+
+def c2_block(args, bem, stream, flush):
+    """The same step on the 20k device, both GPU forms, each the median of 5 runs."""
+    import torch
+    mesh, pts = workload(args, scale=1.0, points=100000)
+    pts_d = torch.tensor(pts, device="cuda")
+    c = bem.Context(mesh, timing=1)
+    res = {}
+
+    def mk(prec, key):
+        def f():
+            u, it, rel = c.solve(prec, tol=TOL)
+            c.surface_field(u[0], prec)
+            phi, E = c.eval_field(u[0], pts_d, prec)
+            res[key] = (u, it, rel, E)
+        return f
+
+    mk(bem.MIXED, "mixed")()
+    c.reset_counters()
+    t32 = events_ms(mk(bem.MIXED, "mixed"), stream, 5, flush)
+    cnt = c.counters()
+    pairs_step = sum(cnt["pairs"]) / 5
+    c.reset_counters()
+    t64 = events_ms(mk(bem.FP64, "fp64"), stream, 5, flush)
+    cnt64 = c.counters()
+    pairs64 = sum(cnt64["pairs"]) / 5
+    u32, it32, rel32, E32 = res["mixed"]
+    u64, it64, rel64, E64 = res["fp64"]
+    c.close()
+    m32, m64 = float(np.median(t32)), float(np.median(t64))
+    return {"workload": workload_name(mesh), "triangles": int(mesh.np_), "eval_points": len(pts),
+            "statistic": "median of 5 runs (CUDA events), L2 flushed before each",
+            "mixed": {"ms_per_step": m32, "runs_ms": t32, "gmres_iters": it32, "relres": rel32[0],
+                      "value": pairs_step / (m32 * 1e-3) / 1e9, "unit": UNIT},
+            "fp64": {"ms_per_step": m64, "runs_ms": t64, "gmres_iters": it64, "relres": rel64[0],
+                     "value": pairs64 / (m64 * 1e-3) / 1e9, "unit": UNIT},
+            "mixed_speedup": m64 / m32,
+            "sigma_rel_l2_mixed_vs_fp64": (torch.linalg.norm(u32[0] - u64[0]) / torch.linalg.norm(u64[0])).item(),
+            "E_rel_mixed_vs_fp64": ((E32 - E64).abs().max() / E64.abs().max()).item()}
+
+
+def e2e_block(args, bem, mesh, pts, dev, flush, dist, world, pairs_step):
+    """The step end to end through the C ABI with host buffers: bem_create from the
+    host mesh, host-to-device copy of the points, solve, surface field, field,
+    device-to-host copy of sigma, E+ and (phi, E)."""
+    import torch
+    M = len(pts)
+    X_h = torch.tensor(pts).pin_memory()
+    phi_h = torch.empty(M, dtype=torch.float64).pin_memory()
+    E_h = torch.empty((M, 3), dtype=torch.float64).pin_memory()
+    Es_h = torch.empty((mesh.np_, 3), dtype=torch.float64).pin_memory()
+    u_h = torch.empty(mesh.n_unknowns, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        c2 = bem.Context(mesh)           # host mesh -> device inside bem_create
+        p_d = X_h.to(dev, non_blocking=True)
+        u, it, rel = c2.solve(bem.MIXED, tol=TOL)
+        Es = c2.surface_field(u[0], bem.MIXED)
+        phi, E = c2.eval_field(u[0], p_d, bem.MIXED)
+        u_h.copy_(u[0], non_blocking=True)
+        Es_h.copy_(Es, non_blocking=True)
+        phi_h.copy_(phi, non_blocking=True)
+        E_h.copy_(E, non_blocking=True)
+        torch.cuda.synchronize()
+        c2.close()
+
+    n_e2e = 2
+    dist_barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        flush.add_(1.0)
+        e2e_step()
+    torch.cuda.synchronize()
+    dist_barrier(dist)
+    e2e_ms = dist_max(dist, (time.perf_counter() - t0) * 1e3 / n_e2e, dev)
+    h2d = mesh.X.size * 8 + mesh.tri.size * 4 + mesh.region.size * 4 + pts.size * 8
+    d2h = mesh.n_unknowns * 8 + mesh.np_ * 24 + M * 32
+    return {"value": world * pairs_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "runs": n_e2e,
+            "includes": "bem_create from host mesh, H2D points, solve, surface field, eval, D2H"}
 
 # ------------------------------------------------------------------ batched family
 def run_batch(args):
@@ -458,7 +621,7 @@ def run_batch(args):
     flops = far_pairs * (FLOPS_PER_PAIR_OP * Q + 8 * nr)
     far_ms = cm["far_ms"] / max(cm["far_timed"], 1)
     props = torch.cuda.get_device_properties(dev)
-    peak, mhz = fp32_peak_tflops(props.multi_processor_count)
+    peak, peak_basis, _ = fp32_peak(bem, props.multi_processor_count)
     achieved = flops / (far_ms * 1e-3) / 1e12
 
     def solve():
@@ -485,6 +648,20 @@ def run_batch(args):
     ms = float(np.mean(times))
     value = (cb["rhs_pairs"] + resid_pairs) / args.steps / (ms * 1e-3) / 1e9
 
+    # the field at box points of every mesh, one persistent launch per chunk of points
+    Mb = args.batch_points
+    bpts = [torch.tensor(mg.device_box_points(Mb, seed=100 + k), device=dev) for k in range(len(ctxs))]
+    u_b = [u[0] for u in us]
+    B.eval_field(u_b, bpts, bem.MIXED)       # warm-up
+    B.reset_counters()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.eval_field(u_b, bpts, bem.MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ev_ms = e0.elapsed_time(e1)
+    ev_pairs = B.counters()["eval_pairs"]
     # field lines: seeds on a sphere of radius 1.05 around the conductor, mixed form
     L = args.seeds
     seeds = [mg.fibonacci_seeds(L, radius=1.05) for _ in ctxs]
@@ -518,8 +695,11 @@ def run_batch(args):
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": None,
                         "kernel": f"k_bfar<{Q},{nr}>: persistent batched FP32 regular pairs, phi+E, {nr} rhs",
-                        "flops_per_launch": flops, "avg_launch_ms": far_ms,
+                        "flops_per_launch": flops, "avg_launch_ms": far_ms, "peak_basis": peak_basis,
                         "flops_basis": f"far pairs x ({FLOPS_PER_PAIR_OP} x {Q} nodes + 8 x {nr} rhs)"},
+           "eval": {"points_per_mesh": Mb, "ms": ev_ms, "pairs": ev_pairs,
+                    "ginteractions_per_s": ev_pairs / (ev_ms * 1e-3) / 1e9,
+                    "call": "bem_batch_eval_field (mixed): one persistent regular-pair launch for all meshes"},
            "trace": {"lines": int(L * len(ctxs)), "ms": tms, "lines_per_s": L * len(ctxs) / (tms * 1e-3),
                      "rk4_steps": steps_total,
                      "status_counts": {int(k): int(v) for k, v in zip(*np.unique(st_all, return_counts=True))},
@@ -542,10 +722,10 @@ def run_trace(args):
     __graft_entry__.build()
     from paper_2003_12663_gb300 import bem
     from paper_2003_12663_gb300 import meshgen as mg
-    mesh = mg.device_mesh(args.scale, seed=2)
+    mesh = mg.device_mesh(args.scale if args.scale is not None else 1.0, seed=2)
     ctx = bem.Context(mesh)
     u, _, _ = ctx.solve(bem.MIXED, tol=TOL)
-    seeds = torch.tensor(mg.fibonacci_seeds(args.lines, radius=1.05))
+    seeds = torch.tensor(mg.fibonacci_seeds(args.lines, radius=args.seed_radius))
     ctx.trace_lines(u[0], seeds[:8], bem.MIXED, max_steps=args.max_steps)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -556,7 +736,8 @@ def run_trace(args):
     ms = e0.elapsed_time(e1)
     steps = int(ns.sum().item())
     Q = ctx.params.far_order ** 2
-    print(json.dumps({"mode": "trace", "triangles": ctx.np, "lines": args.lines, "ms": ms,
+    print(json.dumps({"mode": "trace", "triangles": ctx.np, "lines": args.lines, "seed_radius": args.seed_radius,
+                      "ms": ms,
                       "lines_per_s": args.lines / (ms * 1e-3), "rk4_steps": steps,
                       "field_pair_ops_per_s": steps * 4 * ctx.np * Q / (ms * 1e-3),
                       "status_counts": {int(k): int(v) for k, v in
@@ -752,6 +933,11 @@ def run_report(args):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores, timed
+    on a bounded sample of the same workload.  Each step computes the oracle's pair
+    integrals of 48 seeded collocation rows (the solve's products) and the field of
+    48 seeded evaluation points (the field phase) against all triangles; the line's
+    config names exactly that sample."""
     world, rank, local = dist_setup(args)
     if rank != 0:
         return
@@ -782,13 +968,18 @@ def run_reference(args):
     value = pairs / (ms * 1e-3) / 1e9
     sample = (f"per step: oracle pair integrals of {rows} seeded collocation rows and {ppts} "
               f"evaluation points x {P.N} triangles (FP64, OpenMP)")
+    cfg = {"workload": workload_name(mesh), "triangles": int(mesh.np_), "unknowns": int(mesh.n_unknowns),
+           "counts_sphere_torus_cylinder": list(mesh.info["counts"]),
+           "timed_per_step": f"{rows} collocation rows + {ppts} field points against all {P.N} triangles "
+                             f"(no solve, no full field: a bounded sample of the step's pair integrals)",
+           "far_rule": "3x3 Duffy/Gauss, eta=4", "parallelism": "host cores, rank 0 only"}
     print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                       "dtype": "f64", "data": "synthetic (seeded meshes and points)",
-                      "config": config_of(args, mesh), "impl": "reference",
+                      "config": cfg, "impl": "reference",
                       "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
-                                       "kind": "oracle", "sample": sample},
+                                       "kind": "oracle", "sample": sample, "cpu_model": cpu_model()},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}), flush=True)
 

@@ -70,7 +70,7 @@ enum { BEM_CONDUCTOR = 0, BEM_FLOATING = 1, BEM_DIELECTRIC = 2, BEM_SHEET = 3 };
 enum { BEM_FP64 = 0, BEM_MIXED = 1, BEM_DF = 2 };
 
 typedef struct {
-    int32_t kind;        /* BEM_CONDUCTOR, BEM_FLOATING or BEM_DIELECTRIC */
+    int32_t kind;        /* BEM_CONDUCTOR, BEM_FLOATING, BEM_DIELECTRIC or BEM_SHEET */
     int32_t floating_id; /* BEM_FLOATING, BEM_SHEET: 0 .. n_floating-1, one id per floating body */
     double V0;           /* BEM_CONDUCTOR: prescribed potential (Eq. conductor) */
     double eps_plus;     /* permittivity on the normal's side (Eqs. Jump, Final4, Final3) */
@@ -101,7 +101,14 @@ typedef struct {
     int32_t far32_variant;   /* FP32 regular-pair kernel: 1 scalar, 2 or 4 packed target pairs
                                 per thread; 0 (default): bem_create times the candidates on the
                                 mesh's own matvec and keeps the fastest (N >= 4096; else 2) */
-    int32_t reserved;
+    int32_t adjoint_checkpoint; /* bem_adjoint keeps the state of every line every this many
+                                   RK4 steps and recomputes the steps in between; default 128 */
+    int64_t adjoint_lines;   /* lines bem_adjoint holds at once (more are taken in turns); the
+                                adjoint workspace (checkpoints for this many lines at the default
+                                step limit, one segment of step records, per-line gradient
+                                buffers of at most 64 MiB, the transposed operator's near pairs
+                                by column) is allocated by bem_create; 0: none (bem_adjoint and
+                                bem_matvec_transpose then return BEM_ERR_CAPACITY); default 256 */
 } bem_params;
 
 /* How the iterative refinement of BEM_MIXED forms its residual b - A u.
@@ -124,7 +131,26 @@ typedef struct {
     int64_t far32_variant;      /* FP32 kernel variant in use (1, 2 or 4; not reset) */
     int64_t phi_pairs[3];       /* of pairs, those of product tiles holding only conductor rows,
                                    summed for phi alone (their row equation needs no E) */
+    int64_t chunks32p;          /* 32-triangle chunks the packed FP32 kernel (variants 2, 4) staged,
+                                   summed over its CTAs */
+    int64_t fast_chunks32p;     /* of those, chunks whose every pair with the CTA's targets was
+                                   certainly regular (bounding spheres), summed without classification */
 } bem_counters;
+
+/* The shape the context's FP32 regular-pair kernel runs with, and how it was chosen
+ * (bem_create's tuner: every candidate timed on the mesh's own mixed matvec). */
+typedef struct {
+    int32_t far32_variant;   /* 1 scalar, 2 or 4 packed target pairs per thread */
+    int32_t far32_slots;     /* CTA slots per SM the number of triangle slices aims at */
+    int32_t source;          /* 0 fixed (params.far32_variant, or N < 4096), 1 timed by this
+                                bem_create, 2 taken from the process-wide table (same device, size
+                                bucket and far_order, timed by an earlier context) */
+    int32_t bucket;          /* size bucket floor(2 log2 N) */
+    int32_t n_candidates;    /* candidates timed (source 1) */
+    int32_t cand_variant[9];
+    int32_t cand_slots[9];
+    float cand_ms[9];        /* one mixed matvec of this mesh per candidate */
+} bem_tuning;
 
 typedef struct bem_ctx bem_ctx;
 
@@ -160,6 +186,13 @@ int bem_sync(bem_ctx* ctx);
 
 /* Copy the work counters into *out (host).  Synchronises the stream. */
 int bem_get_counters(bem_ctx* ctx, bem_counters* out);
+
+/* The tuner's choice for this context (host struct).  Never synchronises. */
+int bem_get_tuning(const bem_ctx* ctx, bem_tuning* out);
+
+/* Forget the tuner's process-wide table (the next context of every size bucket times
+ * its candidates again). */
+void bem_clear_tuning_table(void);
 
 /* Zero the work counters. */
 int bem_reset_counters(bem_ctx* ctx);
@@ -236,7 +269,9 @@ int bem_eval_field(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t
  * 8 MiB array in the library's static device memory, which every GPU that loads the
  * library holds until the process exits.  The first call on a device looks up that
  * array's device address (cudaGetSymbolAddress) with the context's device current;
- * make that first call before any stream capture.  All calls on a device share the
+ * make that first call before any stream capture.  The address is kept for the
+ * life of the process: after cudaDeviceReset (or any teardown of the device's
+ * primary context) it is stale, so do not call this entry point again after one.  All calls on a device share the
  * array, so calls whose GPU work overlaps (other streams, other threads, other
  * contexts on the same device) race and give wrong results: order them.  Nothing
  * needs clearing between calls (every partial read is written by the same call).
@@ -273,7 +308,9 @@ void bem_default_trace_params(bem_trace_params* tp);
  * u_dev: device double [>= N]; seeds_dev: device double [L][3]; tp: host, NULL =
  * defaults; outputs (device): K_dev double [L], status_dev int32 [L], nsteps_dev
  * int32 [L] (completed steps), xend_dev double [L][3] (end point), any may be NULL.
- * One CTA per line; precision BEM_FP64 or BEM_MIXED (regular pairs in FP32).
+ * One persistent launch: a CTA of 8 warps traces up to 8 lines, one per warp, whose field
+ * evaluations share the CTA's sweeps over the triangles; precision BEM_FP64 or
+ * BEM_MIXED (regular pairs in FP32).
  */
 int bem_trace_lines(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t L,
                     const double* seeds_dev, const bem_trace_params* tp, double* K_dev,
@@ -284,8 +321,9 @@ int bem_trace_lines(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_
  * column j of A integrates over triangle j the potential of point charges (rows of
  * conductors and floating bodies) and dipoles along n_i (dielectric rows, and the
  * neutrality rows' weights) placed at the centroids.  x_dev, y_dev: device double
- * [N+F].  precision: BEM_FP64 or BEM_MIXED.  The first call builds a column-ordered
- * copy of the near pairs (allocates device memory once).  far_order 2..4.
+ * [N+F].  precision: BEM_FP64 or BEM_MIXED.  Uses the column-ordered copy of the near
+ * pairs that bem_create builds with the adjoint workspace (params.adjoint_lines > 0;
+ * else BEM_ERR_CAPACITY); allocates nothing.  far_order 2..4.
  */
 int bem_matvec_transpose(bem_ctx* ctx, int32_t precision, const double* x_dev, double* y_dev);
 
@@ -296,8 +334,12 @@ int bem_matvec_transpose(bem_ctx* ctx, int32_t precision, const double* x_dev, d
  * objective built on Eq. Breakdowncrit (the paper's outlook names optimisation;
  * the adjoint itself is not in the paper).  u_dev must solve the system for the
  * mesh's V0 (bem_solve, same precision).  The discrete adjoint of what bem_solve
- * and bem_trace_lines compute: the trace is re-run with a tape, reversed step by
- * step (located crossings enter through the implicit function theorem), A^T mu =
+ * and bem_trace_lines compute: the lines are traced again keeping the state at the
+ * start of every params.adjoint_checkpoint-th step; then, from the last segment to
+ * the first, each segment's steps are traced once more from their checkpoint with a
+ * record of every sub-step and reversed step by step (located crossings enter
+ * through the implicit function theorem); the result does not depend on the
+ * checkpoint interval.  A^T mu =
  * dJ/du is solved by GMRES, and -mu^T (dA/dtheta) u + mu^T db/dtheta is summed
  * pair by pair; regular pairs are differentiated on their quadrature nodes, near
  * pairs through the closed form with dual numbers.
@@ -305,9 +347,12 @@ int bem_matvec_transpose(bem_ctx* ctx, int32_t precision, const double* x_dev, d
  * gV0_dev double [nregions] (dJ/dV0 of every conductor region, 0 elsewhere);
  * geps_dev double [nregions][2] (dJ/d eps_plus, dJ/d eps_minus; eps_plus of a
  * floating region enters its neutrality row, and both permittivities of a sheet
- * enter its row of Eq. sheets).  Allocates temporary device memory
- * (the tape: ~88 bytes per step and line) and synchronises.  BEM_ERR_ARG if a line
- * ends on another electrode or in a singular field (status 2 or -1).  far_order 2..4.
+ * enter its row of Eq. sheets).  Allocates nothing: it works in the adjoint workspace
+ * of bem_create (params.adjoint_lines lines at a time, any L), and synchronises.
+ * BEM_ERR_CAPACITY if the context has no adjoint workspace, or if tp->max_steps needs
+ * more checkpoints per line than the workspace holds for even one line.  BEM_ERR_ARG
+ * if a line ends on another electrode or in a singular field (status 2 or -1).
+ * far_order 2..4.
  */
 int bem_adjoint(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t L,
                 const double* seeds_dev, const bem_trace_params* tp, const double* dL_dK_dev,
@@ -320,6 +365,18 @@ int bem_adjoint(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t L,
  */
 int bem_surface_field(bem_ctx* ctx, int32_t precision, const double* u_dev, double* E_dev);
 
+/*
+ * Measured arithmetic peaks of the current CUDA device, the denominators of the
+ * regular-pair kernels' roofline: fused multiply-add chains at full occupancy,
+ * timed with CUDA events (best of three launches, about 0.1 s in all), 2 flops per
+ * multiply-add.  fp32_tflops: the larger of the paired (fma on float2) and scalar
+ * FP32 rates; fp32_scalar_tflops: the scalar rate; fp64_tflops: the FP64 rate.
+ * Outputs are host pointers, any may be NULL.  Allocates and frees a small device
+ * buffer and a private stream; synchronises.  Not part of the paper's method.
+ * Errors: BEM_ERR_CUDA (message in bem_last_error(NULL)).
+ */
+int bem_measure_peaks(double* fp32_tflops, double* fp64_tflops, double* fp32_scalar_tflops);
+
 /* ------------------------------------------------------------------ batches
  * Many meshes (instances) of uneven size with up to four right-hand sides each,
  * served together: the operators are those of bem_matvec / bem_solve /
@@ -329,9 +386,10 @@ int bem_surface_field(bem_ctx* ctx, int32_t precision, const double* u_dev, doub
  *     from an atomic counter; one pass over a pair's quadrature nodes serves all
  *     right-hand sides of its instance.
  *   - bem_batch_solve runs restarted GMRES(m) with right Jacobi scaling on all
- *     systems in lock step; one Arnoldi iteration of all systems is captured once as
- *     a CUDA graph and replayed (Hessenberg columns, rotations and stop tests on
- *     the device).
+ *     systems in lock step; a whole restart cycle (m Arnoldi iterations of all
+ *     systems) is captured once as a CUDA graph and replayed once per cycle, with one
+ *     host synchronisation (Hessenberg columns, rotations and stop tests on the
+ *     device; iterations after every system has stopped do no work).
  *   - bem_batch_trace traces the lines of all instances in one persistent launch.
  * The batch owns its workspace (Krylov bases: (m+1) x (N_i+F_i) doubles per system)
  * and a private stream; every call orders itself after the work already queued on
@@ -346,12 +404,13 @@ typedef struct {
     int64_t far_launches;     /* batched regular-pair launches (graph replays included) */
     int64_t pairs;            /* (target, triangle) pairs those launches covered */
     int64_t rhs_pairs;        /* pairs x right-hand sides */
-    int64_t graph_launches;   /* replays of the Arnoldi-iteration graph */
+    int64_t graph_launches;   /* replays of the restart-cycle graph (one per cycle) */
     int64_t kernel_launches;  /* kernels launched by the batch, graph nodes included */
     int64_t arnoldi_steps;    /* Arnoldi iterations summed over the systems */
     int64_t lines;            /* field lines traced */
     int64_t far_timed;        /* regular-pair launches timed (flags bit 0, bem_batch_matvec) */
     double far_ms;            /* their total time in milliseconds */
+    int64_t eval_pairs;       /* (point, triangle) pairs of the batched field-point launches */
 } bem_batch_counters;
 
 /*
@@ -395,12 +454,29 @@ int bem_batch_solve(bem_batch* b, int32_t precision, const double* const* V0, do
  * u: host array of n device pointers to double [>= N_i]; L: host int64 [n] lines per
  * instance (0 allowed); seeds: host array of n device pointers to double [L_i][3];
  * K, status, nsteps: host arrays of n device pointers (each may be NULL, or the
- * array itself NULL).  One persistent launch; a CTA traces one line at a time.
+ * array itself NULL).  One persistent launch; a CTA of 8 warps traces up to 8 lines at
+ * a time, one per warp, taking lines of one mesh after another.
  * precision BEM_FP64 or BEM_MIXED.  Synchronises.
  */
 int bem_batch_trace(bem_batch* b, int32_t precision, const double* const* u, const int64_t* L,
                     const double* const* seeds, const bem_trace_params* tp, double* const* K,
                     int32_t* const* status, int32_t* const* nsteps);
+
+/*
+ * phi and E at points of every instance (as bem_eval_field), for a family of meshes at
+ * once.  BEM_MIXED: the regular pairs of all instances' points run in ONE persistent
+ * launch per chunk of points (the chunk is the smallest params.max_points of the
+ * contexts; work items of 256 points x a triangle slice common to all instances), in
+ * each context's own far workspace; then each instance's FP64 near pass.  BEM_FP64:
+ * each instance's bem_eval_field in turn.  u: host array of n device pointers to double
+ * [>= N_i]; M: host int64 [n] points per instance (0 allowed); pts: host array of n
+ * device pointers to double [M_i][3]; phi, E: host arrays of n device pointers to
+ * double [M_i] and [M_i][3] (entries, or the arrays, may be NULL).  Allocates nothing;
+ * asynchronous like bem_eval_field.  The paper evaluates one device at a time; this
+ * call serves the batch.
+ */
+int bem_batch_eval_field(bem_batch* b, int32_t precision, const double* const* u, const int64_t* M,
+                         const double* const* pts, double* const* phi, double* const* E);
 
 #ifdef __cplusplus
 }

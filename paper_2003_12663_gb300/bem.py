@@ -48,7 +48,8 @@ class bem_params(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("max_points", ctypes.c_int64),
                 ("timing", ctypes.c_int32), ("residual", ctypes.c_int32),
-                ("far32_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("far32_variant", ctypes.c_int32), ("adjoint_checkpoint", ctypes.c_int32),
+                ("adjoint_lines", ctypes.c_int64)]
 
 
 RESIDUAL_DF, RESIDUAL_FP64 = 0, 1
@@ -65,7 +66,8 @@ class bem_counters(ctypes.Structure):
                 ("pairs", ctypes.c_int64 * 3), ("near_pairs", ctypes.c_int64 * 3),
                 ("far_ms", ctypes.c_double * 3), ("matvecs", ctypes.c_int64 * 3),
                 ("gmres_iters", ctypes.c_int64), ("far32_variant", ctypes.c_int64),
-                ("phi_pairs", ctypes.c_int64 * 3)]
+                ("phi_pairs", ctypes.c_int64 * 3), ("chunks32p", ctypes.c_int64),
+                ("fast_chunks32p", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -75,12 +77,27 @@ class bem_counters(ctypes.Structure):
         return out
 
 
+class bem_tuning(ctypes.Structure):
+    _fields_ = [("far32_variant", ctypes.c_int32), ("far32_slots", ctypes.c_int32),
+                ("source", ctypes.c_int32), ("bucket", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
+                ("cand_variant", ctypes.c_int32 * 9), ("cand_slots", ctypes.c_int32 * 9),
+                ("cand_ms", ctypes.c_float * 9)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {"far32_variant": self.far32_variant, "far32_slots": self.far32_slots,
+                "source": ["fixed", "timed", "table"][self.source], "bucket": self.bucket,
+                "candidates": [{"variant": self.cand_variant[k], "slots": self.cand_slots[k],
+                                "ms": self.cand_ms[k]} for k in range(n)]}
+
+
 class bem_batch_counters(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_int64), ("nrhs", ctypes.c_int64),
                 ("far_launches", ctypes.c_int64), ("pairs", ctypes.c_int64),
                 ("rhs_pairs", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("arnoldi_steps", ctypes.c_int64),
-                ("lines", ctypes.c_int64), ("far_timed", ctypes.c_int64), ("far_ms", ctypes.c_double)]
+                ("lines", ctypes.c_int64), ("far_timed", ctypes.c_int64), ("far_ms", ctypes.c_double),
+                ("eval_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -112,6 +129,9 @@ _SIGS = {
                            _vp, _vp, _vp]),
     "bem_trace_lines": (_i32, [_vp, _i32, _vp, _i64, _vp, ctypes.POINTER(bem_trace_params), _vp,
                                _vp, _vp, _vp]),
+    "bem_measure_peaks": (_i32, [ctypes.POINTER(_dbl)] * 3),
+    "bem_get_tuning": (_i32, [_vp, ctypes.POINTER(bem_tuning)]),
+    "bem_clear_tuning_table": (None, []),
     "bem_batch_create": (_i32, [_pvp, _pvp, _i32, _i32, _i32]),
     "bem_batch_destroy": (_i32, [_vp]),
     "bem_batch_last_error": (ctypes.c_char_p, [_vp]),
@@ -120,6 +140,7 @@ _SIGS = {
     "bem_batch_matvec": (_i32, [_vp, _pvp, _pvp]),
     "bem_batch_solve": (_i32, [_vp, _i32, _pvp, _pvp, _dbl, ctypes.POINTER(_i32),
                                ctypes.POINTER(_dbl)]),
+    "bem_batch_eval_field": (_i32, [_vp, _i32, _pvp, ctypes.POINTER(_i64), _pvp, _pvp, _pvp]),
     "bem_batch_trace": (_i32, [_vp, _i32, _pvp, ctypes.POINTER(_i64), _pvp,
                                ctypes.POINTER(bem_trace_params), _pvp, _pvp, _pvp]),
 }
@@ -228,6 +249,11 @@ class Context:
 
     def reset_counters(self):
         _check(lib().bem_reset_counters(self.h), self.h)
+
+    def tuning(self) -> dict:
+        t = bem_tuning()
+        _check(lib().bem_get_tuning(self.h, ctypes.byref(t)), self.h)
+        return t.as_dict()
 
     def rhs(self, V0=None, nrhs=1):
         t = self._torch
@@ -350,6 +376,19 @@ class Context:
         return A
 
 
+def clear_tuning_table():
+    """bem_clear_tuning_table: the next context of every size bucket times its candidates."""
+    lib().bem_clear_tuning_table()
+
+
+def measure_peaks() -> dict:
+    """bem_measure_peaks on the current device: FP32 (paired and scalar) and FP64
+    multiply-add rates in TFLOP/s."""
+    a, b, c = _dbl(), _dbl(), _dbl()
+    _check(lib().bem_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), None)
+    return {"fp32_tflops": a.value, "fp64_tflops": b.value, "fp32_scalar_tflops": c.value}
+
+
 def _ptr_array(tensors):
     """Host array of device pointers (None -> NULL entries)."""
     return (_vp * len(tensors))(*[None if t is None else t.data_ptr() for t in tensors])
@@ -433,6 +472,19 @@ class Batch:
         if check or rc not in (0, -4):
             self._check(rc)
         return us, np.array(it[:]).reshape(n, nr), np.array(rel[:]).reshape(n, nr)
+
+    def eval_field(self, us, pts, precision=MIXED):
+        """bem_batch_eval_field: lists of (phi, E) per instance for its points."""
+        t = self._torch
+        us = [u.to(device="cuda", dtype=t.float64).reshape(-1).contiguous() for u in us]
+        ps = [(p if isinstance(p, t.Tensor) else t.as_tensor(np.asarray(p))).to(
+            device="cuda", dtype=t.float64).reshape(-1, 3).contiguous() for p in pts]
+        M = (_i64 * len(ps))(*[len(p) for p in ps])
+        phi = [t.empty(len(p), dtype=t.float64, device="cuda") for p in ps]
+        E = [t.empty((len(p), 3), dtype=t.float64, device="cuda") for p in ps]
+        self._check(lib().bem_batch_eval_field(self.h, precision, _ptr_array(us), M, _ptr_array(ps),
+                                               _ptr_array(phi), _ptr_array(E)))
+        return phi, E
 
     def trace(self, us, seeds, precision=MIXED, **tp):
         """Lines of every instance in one launch: lists of K, status, nsteps (device)."""

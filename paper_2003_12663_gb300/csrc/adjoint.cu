@@ -45,9 +45,20 @@ struct StepRec {
     int32_t kind[4];
 };
 
-struct TapeRec {
-    StepRec* tape;
-    int64_t cap;
+// The state of a line at the start of a step: what a resumed trace starts from.
+struct Ckpt {
+    double x[3];
+    double K;
+    int32_t side;
+    int32_t pad;
+};
+
+// Forward recorder: the state at the start of every k-th step (checkpoints) and the
+// number of step records the line produces.
+struct CkptRec {
+    Ckpt* cp;
+    int64_t ncp;
+    int k;
     int64_t n;
     double s0;
     int seed_region;
@@ -55,39 +66,60 @@ struct TapeRec {
     __device__ void step(int64_t st, const double* x, double K, int side)
     {
         n = st + 1;
-        if (st < cap && (threadIdx.x & 31) == 0) {
-            StepRec& r = tape[st];
+        if (st % k == 0 && st / k < ncp && (threadIdx.x & 31) == 0) {
+            Ckpt& c = cp[st / k];
+            c.x[0] = x[0]; c.x[1] = x[1]; c.x[2] = x[2];
+            c.K = K;
+            c.side = side;
+        }
+    }
+    __device__ void sub(int64_t, int, double, int) {}
+};
+
+// Segment recorder: the step records (start state and sub-steps) of steps
+// [step0, step0 + k), from a resumed trace.
+struct SegRec {
+    StepRec* tape;
+    int64_t step0;
+    int k;
+    __device__ void begin(double, int) {}
+    __device__ void step(int64_t st, const double* x, double K, int side)
+    {
+        const int64_t i = st - step0;
+        if (i >= 0 && i < k && (threadIdx.x & 31) == 0) {
+            StepRec& r = tape[i];
             r.x[0] = x[0]; r.x[1] = x[1]; r.x[2] = x[2];
             r.K = K;
             r.side = side;
             r.nsub = 0;
         }
     }
-    __device__ void sub(int64_t st, int k, double sig, int kind)
+    __device__ void sub(int64_t st, int kk, double sig, int kind)
     {
-        if (st < cap && k < 4 && (threadIdx.x & 31) == 0) {
-            tape[st].sig[k] = sig;
-            tape[st].kind[k] = kind;
-            tape[st].nsub = k + 1;
+        const int64_t i = st - step0;
+        if (i >= 0 && i < k && kk < 4 && (threadIdx.x & 31) == 0) {
+            tape[i].sig[kk] = sig;
+            tape[i].kind[kk] = kind;
+            tape[i].nsub = kk + 1;
         }
     }
 };
 
-// forward with a tape (cap 0: count the records only): the persistent tracer
-// launch of bem_trace_lines, with a recorder per line
+// forward with checkpoints: the persistent tracer launch of bem_trace_lines with a
+// checkpoint recorder per line (cp: [L][ncp])
 template <bool F32, int Q>
 __global__ void __launch_bounds__(kLT)
 k_adj_forward(TArgs A, const double* __restrict__ seeds, int64_t L, unsigned long long* __restrict__ next,
-              StepRec* tape, const int64_t* __restrict__ off, const int64_t* __restrict__ cap,
-              int64_t* __restrict__ nrec, double* __restrict__ s0_out, int* __restrict__ sr_out,
-              double* __restrict__ K_out, int32_t* __restrict__ st_out)
+              Ckpt* __restrict__ cp, int64_t ncp, int k, int64_t* __restrict__ nrec,
+              double* __restrict__ s0_out, int* __restrict__ sr_out, double* __restrict__ K_out,
+              int32_t* __restrict__ st_out)
 {
     __shared__ Round R;
     __shared__ TArgs sA;
     __shared__ int s_int[3];
     run_lines<F32, Q>([&](int) { return A; }, [&](int) { return L; }, 1, L, next, sA, R, s_int,
                       [&](const TArgs& a, Round& r, int, int64_t line) {
-                          TapeRec rec{tape ? tape + off[line] : nullptr, tape ? cap[line] : 0, 0, 1.0, -1};
+                          CkptRec rec{cp + line * ncp, ncp, k, 0, 1.0, -1};
                           double K, xe[3];
                           int st;
                           int64_t ns;
@@ -99,6 +131,36 @@ k_adj_forward(TArgs A, const double* __restrict__ seeds, int64_t L, unsigned lon
                               K_out[line] = K;
                               st_out[line] = st;
                           }
+                      });
+}
+
+// segment seg of every line: resume from checkpoint seg and record steps
+// [seg k, seg k + k) into tape[line][0..k); segn[line] = records written
+template <bool F32, int Q>
+__global__ void __launch_bounds__(kLT)
+k_adj_resume(TArgs A, int64_t L, unsigned long long* __restrict__ next, const Ckpt* __restrict__ cp,
+             int64_t ncp, int k, int64_t seg, const int64_t* __restrict__ nrec,
+             const double* __restrict__ s0s, const int* __restrict__ srs, StepRec* __restrict__ tape,
+             int64_t* __restrict__ segn)
+{
+    __shared__ Round R;
+    __shared__ TArgs sA;
+    __shared__ int s_int[3];
+    run_lines<F32, Q>([&](int) { return A; }, [&](int) { return L; }, 1, L, next, sA, R, s_int,
+                      [&](const TArgs& a, Round& r, int, int64_t line) {
+                          const int64_t n = nrec[line], st0 = seg * (int64_t)k;
+                          if (n <= st0) {
+                              if ((threadIdx.x & 31) == 0) segn[line] = 0;
+                              return;
+                          }
+                          const Ckpt c = cp[line * ncp + seg];
+                          double x[3] = {c.x[0], c.x[1], c.x[2]};
+                          double K = c.K;
+                          SegRec rec{tape + line * (int64_t)k, st0, k};
+                          int st;
+                          int64_t ns;
+                          trace_steps<F32, Q>(a, r, x, K, c.side, s0s[line], srs[line], st0, st0 + k, rec, st, ns);
+                          if ((threadIdx.x & 31) == 0) segn[line] = min(n, st0 + k) - st0;
                       });
 }
 
@@ -329,30 +391,26 @@ __device__ __forceinline__ void jmul(const double* J, const double* v, double* o
 
 template <bool F32, int Q>
 __global__ void __launch_bounds__(kT)
-k_adj_backward(TArgs A, int g, const StepRec* __restrict__ tape, const int64_t* __restrict__ off,
-               const int64_t* __restrict__ nrec, const double* __restrict__ s0s,
-               const double* __restrict__ wts, int64_t line0, int64_t nl, double* __restrict__ gu_l,
-               double* __restrict__ gp_l)
+k_adj_backward(TArgs A, int g, const StepRec* __restrict__ tape, int k, const int64_t* __restrict__ segn,
+               const double* __restrict__ s0s, const double* __restrict__ wts, int64_t nl,
+               double* __restrict__ gu_l, double* __restrict__ gp_l, double* __restrict__ lx_l)
 {
     __shared__ double sh[9 * kWarps];
     __shared__ Stage s_st[4][4];
     __shared__ double s_ev[4][12];  // end point (3), and at a crossing E (3) and J (6)
     __shared__ double s_xs[4][4];  // sub-step start x (3) and K
+    // one segment of one line per CTA: the line's gradient buffers and the adjoint of
+    // its state (lx) carry over from the later segments, reversed before this one
     const int64_t b = blockIdx.x;
     if (b >= nl) return;
-    const int64_t line = line0 + b;
     double* gu = gu_l + b * A.np;
     double* gpv = gp_l + b * A.np * 9;
-    for (int64_t j = threadIdx.x; j < A.np; j += kT) {
-        gu[j] = 0.0;
-        for (int i = 0; i < 9; ++i) gpv[9 * j + i] = 0.0;
-    }
-    const double s0 = s0s[line];
-    const double lamK = wts[line];
-    double lx[3] = {0.0, 0.0, 0.0};
-    const StepRec* tp = tape + off[line];
+    const double s0 = s0s[b];
+    const double lamK = wts[b];
+    double lx[3] = {lx_l[3 * b], lx_l[3 * b + 1], lx_l[3 * b + 2]};
+    const StepRec* tp = tape + b * (int64_t)k;
     const double cw[4] = {1.0, 2.0, 2.0, 1.0};
-    for (int64_t r = nrec[line] - 1; r >= 0; --r) {
+    for (int64_t r = segn[b] - 1; r >= 0; --r) {
         const StepRec R = tp[r];
         // recompute the sub-steps with field Jacobians at their stages
         double xs[3] = {R.x[0], R.x[1], R.x[2]}, Ks = R.K;
@@ -472,6 +530,11 @@ k_adj_backward(TArgs A, int g, const StepRec* __restrict__ tape, const int64_t* 
             lx[0] = lxs[0]; lx[1] = lxs[1]; lx[2] = lxs[2];
         }
         __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        lx_l[3 * b] = lx[0];
+        lx_l[3 * b + 1] = lx[1];
+        lx_l[3 * b + 2] = lx[2];
     }
 }
 
@@ -863,14 +926,31 @@ __global__ void k_gather_vertices(int64_t nv, const int64_t* __restrict__ vptr,
     gX[3 * v] = s[0]; gX[3 * v + 1] = s[1]; gX[3 * v + 2] = s[2];
 }
 
-template <class T>
-struct DevBuf {
-    T* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
-    cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, std::max<size_t>(n, 1) * sizeof(T)); }
-};
-
 }  // namespace
+
+// ---------------------------------------------------------------- adjoint workspace
+// Everything bem_adjoint needs, allocated once by bem_create (params.adjoint_lines > 0):
+// checkpoints for `lines` lines at the default step limit, the step records of one
+// segment of a backward batch, per-line gradient buffers (at most 64 MiB), and the
+// buffers of the system gradient.
+struct AdjWork {
+    int64_t lines = 0;      // lines of one forward chunk at the default step limit
+    int k = 128;            // checkpoint interval (steps)
+    int64_t cp_cap = 0;     // checkpoints the store holds
+    int64_t bw = 0;         // lines of one backward batch
+    int splits = 1;         // target/source slices of the system-gradient kernels
+    Ckpt* cp = nullptr;
+    StepRec* tape = nullptr;
+    int64_t *nrec = nullptr, *segn = nullptr;
+    double *s0 = nullptr, *K = nullptr, *gul = nullptr, *gpl = nullptr, *lx = nullptr;
+    int* sr = nullptr;
+    int32_t* st = nullptr;
+    double *gu = nullptr, *gPt = nullptr, *mu = nullptr, *gPs = nullptr, *af = nullptr, *Tf = nullptr;
+    double *pr = nullptr, *pc = nullptr;
+    double2* ceps = nullptr;
+    int32_t* sheet = nullptr;
+    int64_t *vptr = nullptr, *vc = nullptr;
+};
 
 // ---------------------------------------------------------------- transposed matvec
 static int ensure_csc(bem_ctx* c)
@@ -908,7 +988,9 @@ static int ensure_csc(bem_ctx* c)
 
 int matvecT_impl(bem_ctx* c, int precision, const double* v, double* y)
 {
-    if (int rc = ensure_csc(c)) return rc;
+    if (!c->csc_ptr)
+        return set_err(c, BEM_ERR_CAPACITY, "the transposed operator needs the adjoint workspace "
+                       "(bem_create with params.adjoint_lines > 0)");
     const int64_t np = c->np;
     cudaStream_t s = c->stream;
     k_tsrc<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(np, c->row_kind, c->row_aux, c->row_b, c->row_w,
@@ -958,154 +1040,194 @@ extern "C" int bem_matvec_transpose(bem_ctx* c, int32_t precision, const double*
 }
 
 // ---------------------------------------------------------------- bem_adjoint
+template <class T>
+static bool walloc(T** p, size_t n)
+{
+    if (cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
+
+void adjoint_workspace_free(bem_ctx* c)
+{
+    AdjWork* W = c->adj;
+    if (!W) return;
+    void* ptrs[] = {W->cp, W->tape, W->nrec, W->segn, W->s0, W->K, W->gul, W->gpl, W->lx, W->sr, W->st,
+                    W->gu, W->gPt, W->mu, W->gPs, W->af, W->Tf, W->pr, W->pc, W->ceps, W->sheet,
+                    W->vptr, W->vc};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete W;
+    c->adj = nullptr;
+}
+
+// bem_create: the adjoint workspace and the transposed operator's column lists
+int adjoint_workspace_create(bem_ctx* c)
+{
+    if (c->prm.adjoint_lines <= 0) return BEM_OK;
+    if (int rc = ensure_csc(c)) return rc;
+    AdjWork* W = new AdjWork();
+    c->adj = W;
+    const int64_t np = c->np, nv = c->nv;
+    W->k = std::max(1, (int)c->prm.adjoint_checkpoint);
+    W->lines = c->prm.adjoint_lines;
+    bem_trace_params tp;
+    bem_default_trace_params(&tp);
+    W->cp_cap = W->lines * ((tp.max_steps + W->k - 1) / W->k + 1);
+    // backward batch: per-line gradient buffers (80 bytes per triangle) and one segment of
+    // step records per line, each within 64 MiB
+    W->bw = std::max<int64_t>(1, std::min<int64_t>(W->lines, ((int64_t)64 << 20) / (80 * np)));
+    W->bw = std::max<int64_t>(1, std::min<int64_t>(W->bw, ((int64_t)64 << 20) / ((int64_t)W->k * sizeof(StepRec))));
+    const int64_t tiles = (np + 127) / 128;
+    W->splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, (c->num_sms * 8) / std::max<int64_t>(tiles, 1)));
+    const int64_t L = W->lines, nf = std::max(c->nfloat, 1);
+    const int nreg = (int)c->regions.size();
+    bool ok = walloc(&W->cp, W->cp_cap) && walloc(&W->tape, W->bw * W->k) && walloc(&W->nrec, L) &&
+              walloc(&W->segn, W->bw) && walloc(&W->s0, L) && walloc(&W->K, L) &&
+              walloc(&W->gul, W->bw * np) && walloc(&W->gpl, W->bw * 9 * np) && walloc(&W->lx, 3 * W->bw) &&
+              walloc(&W->sr, L) && walloc(&W->st, L) && walloc(&W->gu, c->nunk) && walloc(&W->gPt, 9 * np) &&
+              walloc(&W->mu, c->nunk) && walloc(&W->gPs, 9 * np) && walloc(&W->af, nf) && walloc(&W->Tf, nf) &&
+              walloc(&W->pr, (size_t)W->splits * np * 3) && walloc(&W->pc, (size_t)W->splits * np * 9) &&
+              walloc(&W->ceps, np) && walloc(&W->sheet, nreg) && walloc(&W->vptr, nv + 1) &&
+              walloc(&W->vc, 3 * np);
+    if (!ok) return set_err(c, BEM_ERR_NOMEM, "adjoint workspace allocation failed");
+    cudaStream_t s = c->stream;
+    // per row (ce, em) of the neutrality summand (see k_float_means), per region
+    // whether it is a sheet, per floating body its area; vertex -> (triangle, corner) lists
+    std::vector<double2> h_ceps(np, make_double2(0.0, 0.0));
+    std::vector<double> h_af(nf, 0.0);
+    std::vector<int32_t> h_sheet(nreg, 0);
+    std::vector<double> g(GEO_STRIDE * np);
+    std::vector<int32_t> tri(3 * np);
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(g.data(), c->geo, g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(tri.data(), c->tri, 3 * np * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < np; ++i) {
+        const bem_region& R = c->regions[c->h_region[i]];
+        if (R.kind == BEM_FLOATING || R.kind == BEM_SHEET) h_af[R.floating_id] += g[GEO_STRIDE * i + GEO_AREA];
+        if (R.kind == BEM_FLOATING) h_ceps[i] = make_double2(R.eps_plus, 0.0);
+        if (R.kind == BEM_SHEET) h_ceps[i] = make_double2(R.eps_plus - R.eps_minus, R.eps_minus);
+    }
+    for (int r = 0; r < nreg; ++r) h_sheet[r] = c->regions[r].kind == BEM_SHEET;
+    std::vector<int64_t> vptr(nv + 1, 0), vc(3 * np);
+    for (int64_t q = 0; q < 3 * np; ++q) vptr[tri[q] + 1]++;
+    for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
+    std::vector<int64_t> pos(vptr.begin(), vptr.end() - 1);
+    for (int64_t q = 0; q < 3 * np; ++q) vc[pos[tri[q]]++] = q;
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(W->ceps, h_ceps.data(), np * sizeof(double2), cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(W->af, h_af.data(), nf * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(W->sheet, h_sheet.data(), nreg * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(W->vptr, vptr.data(), (nv + 1) * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(W->vc, vc.data(), 3 * np * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaStreamSynchronize(s));  // the host vectors end here
+    return BEM_OK;
+}
+
 template <bool F32, int Q>
 static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seeds, const double* wts,
                        double* K_out, double* gX, double* gV0, double* geps, double tol)
 {
+    AdjWork& W = *c->adj;
     cudaStream_t s = c->stream;
     const int64_t np = c->np, nv = c->nv;
     const int precision = F32 ? BEM_MIXED : BEM_FP64;
-    // 1. forward: count, allocate the tape, record
-    DevBuf<int64_t> off, cap, nrec;
-    DevBuf<double> s0s, Kf;
-    DevBuf<int> sr;
-    DevBuf<int32_t> stt;
-    if (off.alloc(L) || cap.alloc(L) || nrec.alloc(L) || s0s.alloc(L) || Kf.alloc(L) || sr.alloc(L) ||
-        stt.alloc(L))
-        return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
+    const int k = W.k;
+    // checkpoints per line for this call's step limit, and the lines that fit
+    const int64_t ncp = (A.max_steps + k - 1) / k + 1;
+    const int64_t chunk = std::min<int64_t>(L, W.cp_cap / ncp);
+    if (chunk < 1)
+        return set_err(c, BEM_ERR_CAPACITY, "adjoint: max_steps %lld needs %lld checkpoints per line; the "
+                       "workspace holds %lld", (long long)A.max_steps, (long long)ncp, (long long)W.cp_cap);
     constexpr size_t fsm = field_smem<F32, Q>();
     BEM_CUDA_TRY(c, allow_smem(k_adj_forward<F32, Q>, fsm));
-    const unsigned fgrid = lines_grid(k_adj_forward<F32, Q>, fsm, c->num_sms, L);
-    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), s));
-    k_adj_forward<F32, Q><<<fgrid, kLT, fsm, s>>>(A, seeds, L, c->d_line_next, nullptr, off.p, cap.p, nrec.p,
-                                                  s0s.p, sr.p, Kf.p, stt.p);
-    BEM_LAUNCH_CHECK(c);
-    std::vector<int64_t> h_n(L), h_off(L);
-    std::vector<int32_t> h_st(L);
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(h_n.data(), nrec.p, L * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(h_st.data(), stt.p, L * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
-    int64_t tot = 0;
-    for (int64_t l = 0; l < L; ++l) {
-        if (h_st[l] == 2 || h_st[l] == -1)
-            return set_err(c, BEM_ERR_ARG, "adjoint: line %lld ends with status %d (only r_max, step "
-                           "limit and field floor are differentiated)", (long long)l, h_st[l]);
-        h_off[l] = tot;
-        tot += h_n[l];
-    }
-    DevBuf<StepRec> tape;
-    if (tape.alloc(tot)) return set_err(c, BEM_ERR_NOMEM, "adjoint: tape of %lld steps", (long long)tot);
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(off.p, h_off.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(cap.p, h_n.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), s));
-    k_adj_forward<F32, Q><<<fgrid, kLT, fsm, s>>>(A, seeds, L, c->d_line_next, tape.p, off.p, cap.p, nrec.p,
-                                                  s0s.p, sr.p, Kf.p, stt.p);
-    BEM_LAUNCH_CHECK(c);
-    if (K_out) BEM_CUDA_TRY(c, cudaMemcpyAsync(K_out, Kf.p, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
-
-    // 2. reverse sweep in batches of lines
-    DevBuf<double> gu, gPt;
-    if (gu.alloc(c->nunk) || gPt.alloc(9 * np)) return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
-    BEM_CUDA_TRY(c, cudaMemsetAsync(gu.p, 0, c->nunk * sizeof(double), s));
-    BEM_CUDA_TRY(c, cudaMemsetAsync(gPt.p, 0, 9 * np * sizeof(double), s));
-    const int64_t per_line = 10 * np;
-    const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(L, ((int64_t)64 << 20) / per_line));
-    DevBuf<double> gul, gpl;
-    if (gul.alloc(batch * np) || gpl.alloc(batch * 9 * np))
-        return set_err(c, BEM_ERR_NOMEM, "adjoint: line buffers");
-    for (int64_t l0 = 0; l0 < L; l0 += batch) {
-        const int64_t nl = std::min(batch, L - l0);
-        k_adj_backward<F32, Q><<<(unsigned)nl, kT, 0, s>>>(A, c->g, tape.p, off.p, nrec.p, s0s.p, wts, l0,
-                                                           nl, gul.p, gpl.p);
+    BEM_CUDA_TRY(c, allow_smem(k_adj_resume<F32, Q>, fsm));
+    BEM_CUDA_TRY(c, cudaMemsetAsync(W.gu, 0, c->nunk * sizeof(double), s));
+    BEM_CUDA_TRY(c, cudaMemsetAsync(W.gPt, 0, 9 * np * sizeof(double), s));
+    std::vector<int64_t> h_n(chunk);
+    std::vector<int32_t> h_st(chunk);
+    for (int64_t c0 = 0; c0 < L; c0 += chunk) {
+        const int64_t nc = std::min(chunk, L - c0);
+        // 1. forward: K, status, step-record counts and a checkpoint every k steps
+        const unsigned fgrid = lines_grid(k_adj_forward<F32, Q>, fsm, c->num_sms, nc);
+        BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), s));
+        k_adj_forward<F32, Q><<<fgrid, kLT, fsm, s>>>(A, seeds + 3 * c0, nc, c->d_line_next, W.cp, ncp, k,
+                                                      W.nrec, W.s0, W.sr, W.K, W.st);
         BEM_LAUNCH_CHECK(c);
-        k_sum_lines<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(nl, np, gul.p, gu.p);
-        BEM_LAUNCH_CHECK(c);
-        k_sum_lines<<<(unsigned)((9 * np + 255) / 256), 256, 0, s>>>(nl, 9 * np, gpl.p, gPt.p);
-        BEM_LAUNCH_CHECK(c);
+        if (K_out) BEM_CUDA_TRY(c, cudaMemcpyAsync(K_out + c0, W.K, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        BEM_CUDA_TRY(c, cudaMemcpyAsync(h_n.data(), W.nrec, nc * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA_TRY(c, cudaMemcpyAsync(h_st.data(), W.st, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
+        for (int64_t l = 0; l < nc; ++l)
+            if (h_st[l] == 2 || h_st[l] == -1)
+                return set_err(c, BEM_ERR_ARG, "adjoint: line %lld ends with status %d (only r_max, step "
+                               "limit and field floor are differentiated)", (long long)(c0 + l), h_st[l]);
+        // 2. reverse sweep, a batch of lines at a time, segment by segment from the last:
+        //    each segment is traced again from its checkpoint with a step record, then reversed
+        for (int64_t b0 = 0; b0 < nc; b0 += W.bw) {
+            const int64_t nb = std::min(W.bw, nc - b0);
+            int64_t segs = 0;
+            for (int64_t l = b0; l < b0 + nb; ++l) segs = std::max(segs, (h_n[l] + k - 1) / k);
+            BEM_CUDA_TRY(c, cudaMemsetAsync(W.gul, 0, nb * np * sizeof(double), s));
+            BEM_CUDA_TRY(c, cudaMemsetAsync(W.gpl, 0, nb * 9 * np * sizeof(double), s));
+            BEM_CUDA_TRY(c, cudaMemsetAsync(W.lx, 0, 3 * nb * sizeof(double), s));
+            const unsigned rgrid = lines_grid(k_adj_resume<F32, Q>, fsm, c->num_sms, nb);
+            for (int64_t seg = segs - 1; seg >= 0; --seg) {
+                BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), s));
+                k_adj_resume<F32, Q><<<rgrid, kLT, fsm, s>>>(A, nb, c->d_line_next, W.cp + b0 * ncp, ncp, k, seg,
+                                                             W.nrec + b0, W.s0 + b0, W.sr + b0, W.tape, W.segn);
+                BEM_LAUNCH_CHECK(c);
+                k_adj_backward<F32, Q><<<(unsigned)nb, kT, 0, s>>>(A, c->g, W.tape, k, W.segn, W.s0 + b0,
+                                                                   wts + c0 + b0, nb, W.gul, W.gpl, W.lx);
+                BEM_LAUNCH_CHECK(c);
+            }
+            k_sum_lines<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(nb, np, W.gul, W.gu);
+            BEM_LAUNCH_CHECK(c);
+            k_sum_lines<<<(unsigned)((9 * np + 255) / 256), 256, 0, s>>>(nb, 9 * np, W.gpl, W.gPt);
+            BEM_LAUNCH_CHECK(c);
+        }
     }
 
     // 3. A^T mu = dJ/du
-    DevBuf<double> mu;
-    if (mu.alloc(c->nunk)) return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
     int iters = 0;
     double rel = 0.0;
-    int rc = solve_transpose(c, precision, gu.p, mu.p, tol, &iters, &rel);
+    int rc = solve_transpose(c, precision, W.gu, W.mu, tol, &iters, &rel);
     if (rc && rc != BEM_ERR_NOT_CONVERGED) return rc;
 
     // 4. -mu^T (dA/dX) u, V0 and eps gradients
     rc = matvec_impl(c, precision, 1, A.u, c->wvec, true);  // fills c->field with phi, E_PV at the centroids
     if (rc) return rc;
     const int nreg = (int)c->regions.size();
-    // per row (ce, em) of the neutrality summand (see k_float_means), per region
-    // whether it is a sheet, per floating body its area
-    std::vector<double2> h_ceps(np, make_double2(0.0, 0.0));
-    std::vector<double> h_af(std::max(c->nfloat, 1), 0.0);
-    std::vector<int32_t> h_sheet(nreg, 0);
-    {
-        std::vector<double> g(GEO_STRIDE * np);
-        BEM_CUDA_TRY(c, cudaMemcpyAsync(g.data(), c->geo, g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-        BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < np; ++i) {
-            const bem_region& R = c->regions[c->h_region[i]];
-            if (R.kind == BEM_FLOATING || R.kind == BEM_SHEET) h_af[R.floating_id] += g[GEO_STRIDE * i + GEO_AREA];
-            if (R.kind == BEM_FLOATING) h_ceps[i] = make_double2(R.eps_plus, 0.0);
-            if (R.kind == BEM_SHEET) h_ceps[i] = make_double2(R.eps_plus - R.eps_minus, R.eps_minus);
-        }
-        for (int r = 0; r < nreg; ++r) h_sheet[r] = c->regions[r].kind == BEM_SHEET;
-    }
-    DevBuf<double2> ceps;
-    DevBuf<double> af, Tf, gPs;
-    DevBuf<int32_t> sheet;
-    if (ceps.alloc(np) || af.alloc(h_af.size()) || Tf.alloc(h_af.size()) || gPs.alloc(9 * np) ||
-        sheet.alloc(nreg))
-        return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(ceps.p, h_ceps.data(), np * sizeof(double2), cudaMemcpyHostToDevice, s));
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(af.p, h_af.data(), h_af.size() * 8, cudaMemcpyHostToDevice, s));
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(sheet.p, h_sheet.data(), nreg * 4, cudaMemcpyHostToDevice, s));
     if (c->nfloat > 0) {
-        k_float_means<<<c->nfloat, 256, 0, s>>>(np, c->float_rows, c->float_off, c->geo, A.u, c->field, ceps.p,
-                                                af.p, Tf.p);
+        k_float_means<<<c->nfloat, 256, 0, s>>>(np, c->float_rows, c->float_off, c->geo, A.u, c->field, W.ceps,
+                                                W.af, W.Tf);
         BEM_LAUNCH_CHECK(c);
     }
     const int64_t tiles = (np + 127) / 128;
-    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, (c->num_sms * 8) / std::max<int64_t>(tiles, 1)));
+    const int splits = W.splits;
     const int64_t per = (np + splits - 1) / splits;
-    DevBuf<double> pr, pc;
-    if (pr.alloc((size_t)splits * np * 3) || pc.alloc((size_t)splits * np * 9))
-        return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
     dim3 grid((unsigned)tiles, (unsigned)splits);
     k_sys_rows<F32, Q><<<grid, 128, 0, s>>>(np, c->g, c->geo, c->hdr32, c->hdr64, c->node32, c->node64,
-                                            c->tgt32, c->row_kind, c->row_aux, c->row_b, c->row_w, mu.p, A.u,
-                                            per, pr.p);
+                                            c->tgt32, c->row_kind, c->row_aux, c->row_b, c->row_w, W.mu, A.u,
+                                            per, W.pr);
     BEM_LAUNCH_CHECK(c);
     k_sys_cols<F32, Q><<<grid, 128, 0, s>>>(np, c->g, c->geo, c->hdr32, c->hdr64, c->node32, c->node64,
-                                            c->tgt32, c->row_kind, c->row_aux, c->row_b, c->row_w, mu.p, A.u,
-                                            per, pc.p);
+                                            c->tgt32, c->row_kind, c->row_aux, c->row_b, c->row_w, W.mu, A.u,
+                                            per, W.pc);
     BEM_LAUNCH_CHECK(c);
-    BEM_CUDA_TRY(c, cudaMemcpyAsync(gPs.p, gPt.p, 9 * np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(W.gPs, W.gPt, 9 * np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     k_sys_row_terms<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(
-        np, splits, splits, c->geo, c->row_kind, c->row_aux, c->row_b, c->row_w, mu.p, A.u, c->field,
-        Tf.p, ceps.p, af.p, pr.p, pc.p, gPs.p);
+        np, splits, splits, c->geo, c->row_kind, c->row_aux, c->row_b, c->row_w, W.mu, A.u, c->field,
+        W.Tf, W.ceps, W.af, W.pr, W.pc, W.gPs);
     BEM_LAUNCH_CHECK(c);
-    k_region_grads<<<nreg, 256, 0, s>>>(np, nreg, c->d_region, c->row_kind, c->row_aux, c->geo, mu.p,
-                                         A.u, c->field, af.p, sheet.p, gV0, geps);
+    k_region_grads<<<nreg, 256, 0, s>>>(np, nreg, c->d_region, c->row_kind, c->row_aux, c->geo, W.mu,
+                                         A.u, c->field, W.af, W.sheet, gV0, geps);
     BEM_LAUNCH_CHECK(c);
     if (gX) {
-        // vertex -> (triangle, corner) lists
-        std::vector<int32_t> tri(3 * np);
-        BEM_CUDA_TRY(c, cudaMemcpy(tri.data(), c->tri, 3 * np * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        std::vector<int64_t> vptr(nv + 1, 0), vc(3 * np);
-        for (int64_t k = 0; k < 3 * np; ++k) vptr[tri[k] + 1]++;
-        for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
-        std::vector<int64_t> pos(vptr.begin(), vptr.end() - 1);
-        for (int64_t k = 0; k < 3 * np; ++k) vc[pos[tri[k]]++] = k;
-        DevBuf<int64_t> dvp, dvc;
-        if (dvp.alloc(nv + 1) || dvc.alloc(3 * np)) return set_err(c, BEM_ERR_NOMEM, "adjoint: allocation failed");
-        BEM_CUDA_TRY(c, cudaMemcpyAsync(dvp.p, vptr.data(), (nv + 1) * 8, cudaMemcpyHostToDevice, s));
-        BEM_CUDA_TRY(c, cudaMemcpyAsync(dvc.p, vc.data(), 3 * np * 8, cudaMemcpyHostToDevice, s));
-        k_gather_vertices<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, dvp.p, dvc.p, gPs.p, gX);
+        k_gather_vertices<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, W.vptr, W.vc, W.gPs, gX);
         BEM_LAUNCH_CHECK(c);
-        BEM_CUDA_TRY(c, cudaStreamSynchronize(s));  // the host lists above must outlive the copies
     }
     BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
     return BEM_OK;
@@ -1120,6 +1242,9 @@ extern "C" int bem_adjoint(bem_ctx* c, int32_t precision, const double* u, int64
         return set_err(c, BEM_ERR_ARG, "precision must be BEM_FP64 or BEM_MIXED");
     if (L < 1 || L > 0x7fffffff || !u || !seeds || !dL_dK)
         return set_err(c, BEM_ERR_ARG, "bem_adjoint: need L >= 1 and non-NULL u, seeds, dL_dK");
+    if (!c->adj)
+        return set_err(c, BEM_ERR_CAPACITY, "bem_adjoint needs the adjoint workspace (bem_create with "
+                       "params.adjoint_lines > 0)");
     TArgs A;
     if (int rc = trace_args(c, tp, u, &A)) return rc;
     BEM_CUDA_TRY(c, cudaMemcpyToSymbolAsync(c_ru, c->h_rule_u.data(), c->g * sizeof(double), 0,

@@ -14,10 +14,11 @@
 //   scaling in lock step.  Hessenberg columns, Givens rotations, residual estimates
 //   and the "still iterating" flags live on the device, so one Arnoldi iteration of
 //   all systems (scaling, the batched product, two rounds of classical Gram-Schmidt,
-//   normalisation, rotation, stop test) is a fixed kernel sequence: it is captured
-//   once as a CUDA graph and replayed, its kernels reading the iteration index and
-//   the flags from device memory.  After each replay the host reads one int (the
-//   number of systems still iterating).
+//   normalisation, rotation, stop test) is a fixed kernel sequence.  A whole restart
+//   cycle, m such iterations, is captured once as a CUDA graph and replayed, its
+//   kernels reading the iteration index and the flags from device memory; once no
+//   system iterates, the remaining iterations of the cycle do no work.  After each
+//   replay the host reads one int (the number of systems still iterating).
 // * Iterative refinement as in bem_solve: the correction equations are solved with
 //   the FP32 products above, the residual b - A u with each instance's FP64-accurate
 //   operator (double-FP32 regular pairs by default).
@@ -89,11 +90,121 @@ struct SysState {
 };
 
 // ---------------------------------------------------------------- regular pairs
+// The regular pairs of kBTR targets per thread (tx, ty, tz) with triangles [p0, p1) of
+// one mesh, for NR densities z[q * zs + j]: FP32 node sums, the FP32 classification,
+// per-chunk partials added with Kahan compensation (acc + cmp carries the sum).
+template <int Q, int NR>
+__device__ __forceinline__ void bfar_range(const float* tx, const float* ty, const float* tz, int64_t p0,
+                                           int64_t p1, const float4* __restrict__ hdr,
+                                           const float4* __restrict__ node, const double* __restrict__ z,
+                                           int64_t zs, float4* s_hdr, float4* s_node, float (*s_u)[kBPC],
+                                           float (&acc)[NR][kBTR][4], float (&cmp)[NR][kBTR][4])
+{
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+        for (int r = 0; r < kBTR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[q][r][c] = cmp[q][r][c] = 0.f;
+    for (int64_t c0 = p0; c0 < p1; c0 += kBPC) {
+        const int npc = (int)min((int64_t)kBPC, p1 - c0);
+        __syncthreads();
+        for (int k = tid; k < npc; k += kBT) {
+            s_hdr[k] = hdr[c0 + k];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) s_u[q][k] = __double2float_rn(z[q * zs + c0 + k]);
+        }
+        for (int k = tid; k < npc * Q; k += kBT) s_node[k] = node[c0 * Q + k];
+        __syncthreads();
+        float cp[NR][kBTR][4];
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+#pragma unroll
+            for (int r = 0; r < kBTR; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cp[q][r][c] = 0.f;
+        for (int p = 0; p < npc; ++p) {
+            float ps[kBTR], gx[kBTR], gy[kBTR], gz[kBTR];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const float4 nd = s_node[p * Q + k];
+#pragma unroll
+                for (int r = 0; r < kBTR; ++r) {
+                    const float dx = tx[r] - nd.x, dy = ty[r] - nd.y, dz = tz[r] - nd.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f)));
+                    const float ri = rsqrtf(r2);
+                    const float t = nd.w * ri;
+                    const float t3 = t * (ri * ri);
+                    if (k == 0) {
+                        ps[r] = t;
+                        gx[r] = t3 * dx; gy[r] = t3 * dy; gz[r] = t3 * dz;
+                    } else {
+                        ps[r] += t;
+                        gx[r] = fmaf(t3, dx, gx[r]);
+                        gy[r] = fmaf(t3, dy, gy[r]);
+                        gz[r] = fmaf(t3, dz, gz[r]);
+                    }
+                }
+            }
+            const float4 h = s_hdr[p];
+#pragma unroll
+            for (int r = 0; r < kBTR; ++r) {
+                const bool far = is_far32(tx[r], ty[r], tz[r], h);
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    const float m = far ? s_u[q][p] : 0.f;
+                    cp[q][r][0] = fmaf(m, ps[r], cp[q][r][0]);
+                    cp[q][r][1] = fmaf(m, gx[r], cp[q][r][1]);
+                    cp[q][r][2] = fmaf(m, gy[r], cp[q][r][2]);
+                    cp[q][r][3] = fmaf(m, gz[r], cp[q][r][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+#pragma unroll
+            for (int r = 0; r < kBTR; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float y = cp[q][r][c] - cmp[q][r][c];
+                    const float t = acc[q][r][c] + y;
+                    cmp[q][r][c] = (t - acc[q][r][c]) - y;
+                    acc[q][r][c] = t;
+                }
+    }
+}
+
+// Take work items from the queue: thread 0 draws an item and finds its instance by
+// binary search in item_off; returns the item (>= total: none left) to every thread.
+__device__ __forceinline__ long long draw_item(unsigned long long* queue, const int64_t* item_off, int ninst,
+                                               int64_t total, long long* s_item, int* s_inst, int& inst)
+{
+    if (threadIdx.x == 0) {
+        const long long it = (long long)atomicAdd(queue, 1ull);
+        int lo = 0;
+        if (it < total) {
+            int hi = ninst - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (item_off[mid] <= it) lo = mid; else hi = mid - 1;
+            }
+        }
+        *s_item = it;
+        *s_inst = lo;
+    }
+    __syncthreads();
+    const long long item = *s_item;
+    inst = *s_inst;
+    __syncthreads();  // every thread holds the item before thread 0 takes the next
+    return item;
+}
+
 template <int Q, int NR>
 __global__ void __launch_bounds__(kBT)
 k_bfar(const Inst* __restrict__ insts, int ninst, const int64_t* __restrict__ item_off,
        int64_t total, unsigned long long* __restrict__ queue, const int* __restrict__ mask,
-       unsigned long long* __restrict__ pairs)
+       unsigned long long* __restrict__ pairs, const int* __restrict__ live)
 {
     __shared__ float4 s_hdr[kBPC];
     __shared__ float4 s_node[kBPC * Q];
@@ -101,41 +212,24 @@ k_bfar(const Inst* __restrict__ insts, int ninst, const int64_t* __restrict__ it
     __shared__ long long s_item;
     __shared__ int s_inst;
     const int tid = threadIdx.x;
+    // inside the Arnoldi graph: once no system iterates, the rest of the cycle's
+    // iterations return at once (live = the count of iterating systems)
+    if (live && *live == 0) return;
     for (;;) {
-        if (tid == 0) {
-            long long it = (long long)atomicAdd(queue, 1ull);
-            int lo = 0;
-            if (it < total) {
-                int hi = ninst - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (item_off[mid] <= it) lo = mid; else hi = mid - 1;
-                }
-                bool any = false;
-#pragma unroll
-                for (int q = 0; q < NR; ++q) any = any || mask[lo * NR + q] != 0;
-                if (!any) it = -1;  // no system of this instance needs the product
-            }
-            s_item = it;
-            s_inst = lo;
-        }
-        __syncthreads();
-        const long long item = s_item;
-        const int ii = s_inst;
-        __syncthreads();  // every thread holds the item before thread 0 takes the next
+        int ii;
+        const long long item = draw_item(queue, item_off, ninst, total, &s_item, &s_inst, ii);
         if (item >= total) break;
-        if (item < 0) continue;
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) any = any || mask[ii * NR + q] != 0;
+        if (!any) continue;  // no system of this instance needs the product
 
         const Inst& I = insts[ii];
-        const int64_t np = I.np, n = I.n;
+        const int64_t np = I.np;
         const int64_t local = item - item_off[ii];
         const int64_t tile = local / I.splits, split = local - tile * I.splits;
         const int64_t base = tile * kTile;
         const int64_t p0 = split * I.slice, p1 = min(np, p0 + I.slice);
-        const float4* __restrict__ hdr = I.hdr32;
-        const float4* __restrict__ node = I.node32;
-        const double* __restrict__ z = I.z;
-
         float tx[kBTR], ty[kBTR], tz[kBTR];
 #pragma unroll
         for (int r = 0; r < kBTR; ++r) {
@@ -143,79 +237,7 @@ k_bfar(const Inst* __restrict__ insts, int ninst, const int64_t* __restrict__ it
             tx[r] = v.x; ty[r] = v.y; tz[r] = v.z;
         }
         float acc[NR][kBTR][4], cmp[NR][kBTR][4];
-#pragma unroll
-        for (int q = 0; q < NR; ++q)
-#pragma unroll
-            for (int r = 0; r < kBTR; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[q][r][c] = cmp[q][r][c] = 0.f;
-
-        for (int64_t c0 = p0; c0 < p1; c0 += kBPC) {
-            const int npc = (int)min((int64_t)kBPC, p1 - c0);
-            __syncthreads();
-            for (int k = tid; k < npc; k += kBT) {
-                s_hdr[k] = hdr[c0 + k];
-#pragma unroll
-                for (int q = 0; q < NR; ++q) s_u[q][k] = __double2float_rn(z[q * n + c0 + k]);
-            }
-            for (int k = tid; k < npc * Q; k += kBT) s_node[k] = node[c0 * Q + k];
-            __syncthreads();
-            float cp[NR][kBTR][4];
-#pragma unroll
-            for (int q = 0; q < NR; ++q)
-#pragma unroll
-                for (int r = 0; r < kBTR; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) cp[q][r][c] = 0.f;
-            for (int p = 0; p < npc; ++p) {
-                float ps[kBTR], gx[kBTR], gy[kBTR], gz[kBTR];
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const float4 nd = s_node[p * Q + k];
-#pragma unroll
-                    for (int r = 0; r < kBTR; ++r) {
-                        const float dx = tx[r] - nd.x, dy = ty[r] - nd.y, dz = tz[r] - nd.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f)));
-                        const float ri = rsqrtf(r2);
-                        const float t = nd.w * ri;
-                        const float t3 = t * (ri * ri);
-                        if (k == 0) {
-                            ps[r] = t;
-                            gx[r] = t3 * dx; gy[r] = t3 * dy; gz[r] = t3 * dz;
-                        } else {
-                            ps[r] += t;
-                            gx[r] = fmaf(t3, dx, gx[r]);
-                            gy[r] = fmaf(t3, dy, gy[r]);
-                            gz[r] = fmaf(t3, dz, gz[r]);
-                        }
-                    }
-                }
-                const float4 h = s_hdr[p];
-#pragma unroll
-                for (int r = 0; r < kBTR; ++r) {
-                    const bool far = is_far32(tx[r], ty[r], tz[r], h);
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) {
-                        const float m = far ? s_u[q][p] : 0.f;
-                        cp[q][r][0] = fmaf(m, ps[r], cp[q][r][0]);
-                        cp[q][r][1] = fmaf(m, gx[r], cp[q][r][1]);
-                        cp[q][r][2] = fmaf(m, gy[r], cp[q][r][2]);
-                        cp[q][r][3] = fmaf(m, gz[r], cp[q][r][3]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < NR; ++q)
-#pragma unroll
-                for (int r = 0; r < kBTR; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {  // Kahan: acc + cmp carries the running sum
-                        const float y = cp[q][r][c] - cmp[q][r][c];
-                        const float t = acc[q][r][c] + y;
-                        cmp[q][r][c] = (t - acc[q][r][c]) - y;
-                        acc[q][r][c] = t;
-                    }
-        }
+        bfar_range<Q, NR>(tx, ty, tz, p0, p1, I.hdr32, I.node32, I.z, I.n, s_hdr, s_node, s_u, acc, cmp);
         if (tid == 0)
             atomicAdd(pairs, (unsigned long long)(min((int64_t)kTile, np - base) * (p1 - p0)));
 #pragma unroll
@@ -229,6 +251,62 @@ k_bfar(const Inst* __restrict__ insts, int ninst, const int64_t* __restrict__ it
                     for (int c = 0; c < 4; ++c) o[c] = (double)acc[q][r][c] - (double)cmp[q][r][c];
                 }
             }
+    }
+}
+
+// Field points of one instance for bem_batch_eval_field (device view).
+struct PInst {
+    const double* pts;   // [M][3]
+    const double* u;     // [>= np]
+    const float4* hdr32;
+    const float4* node32;
+    double* part;        // [splits][M][4]: the context's far workspace
+    int64_t M, np, splits, slice;
+};
+
+// The regular pairs of every instance's field points in one persistent launch:
+// work items (instance, tile of kTile points, slice of triangles).
+template <int Q>
+__global__ void __launch_bounds__(kBT)
+k_bfar_pts(const PInst* __restrict__ insts, int ninst, const int64_t* __restrict__ item_off, int64_t total,
+           unsigned long long* __restrict__ queue, unsigned long long* __restrict__ pairs)
+{
+    __shared__ float4 s_hdr[kBPC];
+    __shared__ float4 s_node[kBPC * Q];
+    __shared__ float s_u[1][kBPC];
+    __shared__ long long s_item;
+    __shared__ int s_inst;
+    const int tid = threadIdx.x;
+    for (;;) {
+        int ii;
+        const long long item = draw_item(queue, item_off, ninst, total, &s_item, &s_inst, ii);
+        if (item >= total) break;
+        const PInst& I = insts[ii];
+        const int64_t local = item - item_off[ii];
+        const int64_t tile = local / I.splits, split = local - tile * I.splits;
+        const int64_t base = tile * kTile;
+        const int64_t p0 = split * I.slice, p1 = min(I.np, p0 + I.slice);
+        float tx[kBTR], ty[kBTR], tz[kBTR];
+#pragma unroll
+        for (int r = 0; r < kBTR; ++r) {
+            const int64_t t = min(base + r * kBT + tid, I.M - 1);
+            tx[r] = __double2float_rn(I.pts[3 * t]);
+            ty[r] = __double2float_rn(I.pts[3 * t + 1]);
+            tz[r] = __double2float_rn(I.pts[3 * t + 2]);
+        }
+        float acc[1][kBTR][4], cmp[1][kBTR][4];
+        bfar_range<Q, 1>(tx, ty, tz, p0, p1, I.hdr32, I.node32, I.u, 0, s_hdr, s_node, s_u, acc, cmp);
+        if (tid == 0)
+            atomicAdd(pairs, (unsigned long long)(min((int64_t)kTile, I.M - base) * (p1 - p0)));
+#pragma unroll
+        for (int r = 0; r < kBTR; ++r) {
+            const int64_t t = base + r * kBT + tid;
+            if (t < I.M) {
+                double* o = I.part + ((int64_t)split * I.M + t) * 4;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) o[c] = (double)acc[0][r][c] - (double)cmp[0][r][c];
+            }
+        }
     }
 }
 
@@ -635,6 +713,9 @@ struct bem_batch {
     tcore::TArgs* d_targs = nullptr;
     int64_t* d_loff = nullptr;
     void** d_tptr = nullptr;                // [4][n]: seeds, K, status, nsteps
+    PInst* d_pinst = nullptr;               // [n] field points of bem_batch_eval_field
+    int64_t* d_pitem_off = nullptr;         // [n+1]
+    unsigned long long* d_epairs = nullptr; // pairs of the batched field-point launches
     std::vector<void*> allocs;
     cudaGraphExec_t graph = nullptr;
     int graph_kernels = 0;
@@ -777,7 +858,8 @@ extern "C" int bem_batch_create(bem_batch** out, bem_ctx* const* ctxs, int32_t n
          dalloc(b, &b->d_item_off, n + 1) && dalloc(b, &b->d_queue, 1) && dalloc(b, &b->d_lnext, n) && dalloc(b, &b->d_pairs, 1) &&
          dalloc(b, &b->d_j, 1) && dalloc(b, &b->d_count, 1) && dalloc(b, &b->d_alive, ns) &&
          dalloc(b, &b->d_mask, ns) && dalloc(b, &b->d_all, ns) && dalloc(b, &b->d_upd, ns) &&
-         dalloc(b, &b->d_targs, n) && dalloc(b, &b->d_loff, n + 1) && dalloc(b, &b->d_tptr, 4 * (size_t)n);
+         dalloc(b, &b->d_targs, n) && dalloc(b, &b->d_loff, n + 1) && dalloc(b, &b->d_tptr, 4 * (size_t)n) &&
+         dalloc(b, &b->d_pinst, n) && dalloc(b, &b->d_pitem_off, n + 1) && dalloc(b, &b->d_epairs, 1);
     if (!ok || cudaMallocHost((void**)&b->h_count, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         batch_free(b);
@@ -790,7 +872,8 @@ extern "C" int bem_batch_create(bem_batch** out, bem_ctx* const* ctxs, int32_t n
         cudaMemcpy(b->d_item_off, item_off.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_all, ones.data(), ns * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_st, b->h_st.data(), ns * sizeof(SysState), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->d_pairs, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMemset(b->d_pairs, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(b->d_epairs, 0, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         batch_free(b);
         return BEM_ERR_CUDA;
@@ -812,10 +895,12 @@ extern "C" const char* bem_batch_last_error(const bem_batch* b) { return b ? b->
 extern "C" int bem_batch_get_counters(bem_batch* b, bem_batch_counters* out)
 {
     if (!b || !out) return BEM_ERR_ARG;
-    unsigned long long p = 0;
+    unsigned long long p = 0, ep = 0;
     BB_TRY(b, cudaStreamSynchronize(b->stream));
     BB_TRY(b, cudaMemcpy(&p, b->d_pairs, sizeof(p), cudaMemcpyDeviceToHost));
+    BB_TRY(b, cudaMemcpy(&ep, b->d_epairs, sizeof(ep), cudaMemcpyDeviceToHost));
     b->cnt.pairs = (int64_t)p;
+    b->cnt.eval_pairs = (int64_t)ep;
     b->cnt.rhs_pairs = (int64_t)p * b->nr;
     *out = b->cnt;
     return BEM_OK;
@@ -826,6 +911,7 @@ extern "C" int bem_batch_reset_counters(bem_batch* b)
     if (!b) return BEM_ERR_ARG;
     BB_TRY(b, cudaStreamSynchronize(b->stream));
     BB_TRY(b, cudaMemset(b->d_pairs, 0, sizeof(unsigned long long)));
+    BB_TRY(b, cudaMemset(b->d_epairs, 0, sizeof(unsigned long long)));
     const int64_t ni = b->cnt.n_instances, nr = b->cnt.nrhs;
     b->cnt = bem_batch_counters{};
     b->cnt.n_instances = ni;
@@ -851,8 +937,9 @@ int leave(bem_batch* b)
     return BEM_OK;
 }
 
-// W = A Z for the systems in mask (FP32 regular pairs, FP64 near pairs)
-int apply(bem_batch* b, const int* mask, bool timed)
+// W = A Z for the systems in mask (FP32 regular pairs, FP64 near pairs); live
+// (nullable): device count of iterating systems, 0 skips the regular pairs
+int apply(bem_batch* b, const int* mask, bool timed, const int* live = nullptr)
 {
     cudaStream_t s = b->stream;
     BB_TRY(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), s));
@@ -863,7 +950,7 @@ int apply(bem_batch* b, const int* mask, bool timed)
 #define BF(G, QQ, NR)                                                                          \
     case G * 8 + NR:                                                                           \
         k_bfar<QQ, NR><<<grid, kBT, 0, s>>>(b->d_inst, b->ninst, b->d_item_off, b->total_items, \
-                                             b->d_queue, mask, b->d_pairs);                    \
+                                             b->d_queue, mask, b->d_pairs, live);              \
         break;
         BF(2, 4, 1) BF(2, 4, 2) BF(2, 4, 3) BF(2, 4, 4)
         BF(3, 9, 1) BF(3, 9, 2) BF(3, 9, 3) BF(3, 9, 4)
@@ -898,7 +985,7 @@ int arnoldi_iteration(bem_batch* b)
     const dim3 gv(nblk(b->maxn), ns);
     k_bjac<<<gv, 256, 0, s>>>(b->d_inst, b->d_sys, b->d_alive, b->d_j);
     BB_LAUNCH(b);
-    if (int rc = apply(b, b->d_alive, false)) return rc;
+    if (int rc = apply(b, b->d_alive, false, b->d_count)) return rc;
     for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
         k_bdots<<<dim3(m + 1, ns), 256, 0, s>>>(b->d_sys, b->d_alive, b->d_j);
         BB_LAUNCH(b);
@@ -911,16 +998,25 @@ int arnoldi_iteration(bem_batch* b)
     BB_LAUNCH(b);
     k_bgivens<<<1, 256, 0, s>>>(b->d_sys, b->d_alive, b->d_st, ns, b->d_j, m, b->max_it, b->d_count);
     BB_LAUNCH(b);
-    BB_TRY(b, cudaMemcpyAsync(b->h_count, b->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
     return BEM_OK;
 }
 
+// The graph of one whole restart cycle: m Arnoldi iterations of every system (the
+// kernels read the iteration index and the flags from device memory, and once no
+// system iterates the rest of the cycle does no work), then the count of systems
+// still iterating copied to the host.  One replay and one synchronisation per cycle.
 int ensure_graph(bem_batch* b)
 {
     if (b->graph) return BEM_OK;
     const int64_t k0 = b->cnt.kernel_launches, f0 = b->cnt.far_launches;
     BB_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = arnoldi_iteration(b);
+    int rc = BEM_OK;
+    for (int j = 0; j < b->m && !rc; ++j) rc = arnoldi_iteration(b);
+    if (!rc) {
+        const cudaError_t ec = cudaMemcpyAsync(b->h_count, b->d_count, sizeof(int), cudaMemcpyDeviceToHost,
+                                               b->stream);
+        if (ec != cudaSuccess) rc = berr(b, BEM_ERR_CUDA, "capture of the count copy failed");
+    }
     cudaGraph_t gph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->stream, &gph);
     // captured launches do not run now: they are counted per replay instead
@@ -992,15 +1088,13 @@ int gmres(bem_batch* b, std::vector<int> need, const std::vector<double>& tol)
         k_bstart<<<gv, 256, 0, s>>>(b->d_sys, b->d_mask, b->d_st, b->d_alive, m, b->max_it);
         BB_LAUNCH(b);
         BB_TRY(b, cudaMemsetAsync(b->d_j, 0, sizeof(int), s));
-        *b->h_count = 1;
-        for (int j = 0; j < m; ++j) {  // k_bgivens stops every system by j = m
-            BB_TRY(b, cudaGraphLaunch(b->graph, s));
-            BB_TRY(b, cudaStreamSynchronize(s));
-            ++b->cnt.graph_launches;
-            b->cnt.kernel_launches += b->graph_kernels;
-            ++b->cnt.far_launches;
-            if (*b->h_count == 0) break;
-        }
+        BB_TRY(b, cudaMemsetAsync(b->d_count, 1, sizeof(int), s));  // nonzero: the cycle starts
+        // one replay runs the whole cycle; k_bgivens stops every system by j = m
+        BB_TRY(b, cudaGraphLaunch(b->graph, s));
+        BB_TRY(b, cudaStreamSynchronize(s));
+        ++b->cnt.graph_launches;
+        b->cnt.kernel_launches += b->graph_kernels;
+        b->cnt.far_launches += m;
         k_bsolve<<<nblk(ns, 128), 128, 0, s>>>(b->d_sys, b->d_st, ns, m);
         BB_LAUNCH(b);
         k_bupdate<<<gv, 256, 0, s>>>(b->d_inst, b->d_sys, b->d_st);
@@ -1195,5 +1289,93 @@ extern "C" int bem_batch_trace(bem_batch* b, int32_t precision, const double* co
     b->cnt.lines += total;
     // the host arrays A, loff, ptrs die on return: wait until the copies have run
     BB_TRY(b, cudaStreamSynchronize(s));
+    return leave(b);
+}
+
+// ---------------------------------------------------------------- field at points
+// Mixed form: every instance's points in chunks of the smallest max_points of the
+// contexts; per chunk ONE persistent launch of the regular pairs of all instances
+// (items of kTile points x a triangle slice common to all instances, at most four
+// slices per instance, written into each context's own far workspace), then each
+// instance's deferred FP64 near pass (the kernel of bem_eval_field).  FP64 form: each
+// instance's bem_eval_field in turn.
+extern "C" int bem_batch_eval_field(bem_batch* b, int32_t precision, const double* const* u,
+                                    const int64_t* M, const double* const* pts, double* const* phi,
+                                    double* const* E)
+{
+    if (!b) return BEM_ERR_ARG;
+    if (precision != BEM_FP64 && precision != BEM_MIXED)
+        return berr(b, BEM_ERR_ARG, "bem_batch_eval_field: precision must be BEM_FP64 or BEM_MIXED");
+    if (!u || !M || !pts) return berr(b, BEM_ERR_ARG, "bem_batch_eval_field: NULL array");
+    const int n = b->ninst;
+    int64_t Mmax = 0, CH = INT64_MAX, npmax = 0;
+    for (int i = 0; i < n; ++i) {
+        if (M[i] < 0 || (M[i] > 0 && (!u[i] || !pts[i])))
+            return berr(b, BEM_ERR_ARG, "bem_batch_eval_field: bad M or NULL pointer");
+        Mmax = std::max(Mmax, M[i]);
+        CH = std::min<int64_t>(CH, b->ctx[i]->prm.max_points);
+        npmax = std::max(npmax, b->ctx[i]->np);
+    }
+    if (precision == BEM_FP64) {
+        for (int i = 0; i < n; ++i) {
+            const int rc = bem_eval_field(b->ctx[i], BEM_FP64, u[i], M[i], pts[i], phi ? phi[i] : nullptr,
+                                          E ? E[i] : nullptr);
+            if (rc) return berr(b, rc, bem_last_error(b->ctx[i]));
+        }
+        return BEM_OK;
+    }
+    // a slice length common to all instances: at most four slices of the largest mesh
+    const int64_t slice = std::max<int64_t>(kBPC, ((npmax + 3) / 4 + kBPC - 1) / kBPC * kBPC);
+    if (int rc = enter(b)) return rc;
+    cudaStream_t s = b->stream;
+    std::vector<PInst> pi(n);
+    std::vector<int64_t> off(n + 1);
+    for (int64_t m0 = 0; m0 < Mmax; m0 += CH) {
+        off[0] = 0;
+        for (int i = 0; i < n; ++i) {
+            bem_ctx* c = b->ctx[i];
+            PInst& P = pi[i];
+            P.M = std::max<int64_t>(0, std::min(CH, M[i] - m0));
+            P.pts = P.M > 0 ? pts[i] + 3 * m0 : nullptr;
+            P.u = u[i];
+            P.hdr32 = c->hdr32;
+            P.node32 = c->node32;
+            P.part = c->part;
+            P.np = c->np;
+            P.slice = slice;
+            P.splits = (c->np + slice - 1) / slice;
+            if ((size_t)P.splits * P.M * 4 > c->part_cap)
+                return berr(b, BEM_ERR_CAPACITY, "bem_batch_eval_field: far workspace too small");
+            off[i + 1] = off[i] + ((P.M + kTile - 1) / kTile) * P.splits;
+        }
+        const int64_t total = off[n];
+        if (total == 0) continue;
+        BB_TRY(b, cudaMemcpyAsync(b->d_pinst, pi.data(), n * sizeof(PInst), cudaMemcpyHostToDevice, s));
+        BB_TRY(b, cudaMemcpyAsync(b->d_pitem_off, off.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        BB_TRY(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), s));
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(total, (int64_t)b->num_sms * 4));
+        switch (b->g) {
+            case 2: k_bfar_pts<4><<<grid, kBT, 0, s>>>(b->d_pinst, n, b->d_pitem_off, total, b->d_queue, b->d_epairs); break;
+            case 3: k_bfar_pts<9><<<grid, kBT, 0, s>>>(b->d_pinst, n, b->d_pitem_off, total, b->d_queue, b->d_epairs); break;
+            default: k_bfar_pts<16><<<grid, kBT, 0, s>>>(b->d_pinst, n, b->d_pitem_off, total, b->d_queue, b->d_epairs); break;
+        }
+        BB_LAUNCH(b);
+        ++b->cnt.far_launches;
+        if (int rc = leave(b)) return rc;
+        // the near pass of each instance on the contexts' stream, after the launch above
+        for (int i = 0; i < n; ++i) {
+            const PInst& P = pi[i];
+            if (P.M == 0) continue;
+            const int rc = launch_points_near(b->ctx[i], BEM_MIXED, P.M, P.pts, P.u, P.part, (int)P.splits,
+                                              phi && phi[i] ? phi[i] + m0 : nullptr,
+                                              E && E[i] ? E[i] + 3 * m0 : nullptr);
+            if (rc) return berr(b, rc, bem_last_error(b->ctx[i]));
+            ++b->cnt.kernel_launches;
+        }
+        // the next chunk's launch reuses the contexts' far workspaces: order it after
+        // the near passes
+        if (int rc = enter(b)) return rc;
+    }
+    // (pi and off are pageable: each copy has taken its bytes before it returns)
     return leave(b);
 }

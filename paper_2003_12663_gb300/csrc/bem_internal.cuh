@@ -28,6 +28,8 @@ constexpr int kMaxRhs = 4;            // right-hand sides per matvec launch
 constexpr int kPrecDF = BEM_DF;       // regular pairs in double-FP32 arithmetic
 constexpr double kInv4Pi = 0.07957747154594767;  // 1/(4 pi)
 
+struct AdjWork;  // adjoint.cu: the workspace of bem_adjoint
+
 struct bem_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -52,6 +54,8 @@ struct bem_ctx {
     float4* qnode = nullptr;      // [np][Q] FP32 nodes with sigma folded into w (per call)
     float4* chunk_sph = nullptr;  // [np/32 rounded up] bounding sphere of 32 triangles' near zones
     int far32_tp = 2;             // FP32 kernel variant: 1 scalar, 2 or 4 packed target pairs
+    int far_slots = 4;            // CTA slots per SM the FP32 kernel's slice count aims at (tuned)
+    bem_tuning tune{};            // what the tuner chose and measured
     int64_t phi_tile_targets = 0; // centroid targets in tiles of conductor rows only (packed variant)
     float4* nrm32 = nullptr;      // [np] (unit normal in FP32, region index as int bits): field lines
     float* u32 = nullptr;         // [np] density rounded to FP32 for the field-line integrator
@@ -110,13 +114,20 @@ struct bem_ctx {
     // work counters (bem_counters) and optional kernel timing
     bem_counters cnt{};
     int64_t nnz_prec[3] = {0, 0, 0};          // near pairs of the centroids per pass
-    unsigned long long* d_near_count = nullptr;  // [2] near pairs met by the point kernels
+    unsigned long long* d_near_count = nullptr;  // [4] near pairs met by the point kernels (FP64, FP32);
+                                                 // chunks of k_far32p, of which all-regular
     std::vector<cudaEvent_t> ev0, ev1;        // timing pool: start / stop of far launches
     std::vector<int> ev_prec;
     size_t ev_used = 0;
 
+    AdjWork* adj = nullptr;        // adjoint workspace (params.adjoint_lines > 0)
+
     std::string err;
 };
+
+// adjoint.cu: the adjoint workspace, allocated by bem_create and freed with the context
+int adjoint_workspace_create(bem_ctx* ctx);
+void adjoint_workspace_free(bem_ctx* ctx);
 
 // timing of the regular-pair launches (setup.cu)
 void timing_begin(bem_ctx* ctx, int precision);

@@ -168,7 +168,10 @@ __device__ void tri_cf_t(const T* v, const T* x, bool own, T& S, T* G)
             f = log1p(L * (r0 + r1 - s0 - s1) / ((r0 + r1) * (r1 - s1)));
         else
             f = log((r1 + s1) * (r0 - s0) / (d * d + h * h));
-        if (val(d) != 0.0) sdf = sdf + d * f;
+        // d f vanishes where d does, but its derivative f d' does not (a point whose
+        // projection lies on the edge's line outside the edge); only on the edge itself
+        // is f infinite (a singular field)
+        if (isfinite(val(f))) sdf = sdf + d * f;
         fx = fx + mx * f;
         fy = fy + my * f;
         fz = fz + mz * f;

@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(kThreads)
 k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_t M,
          const float4* __restrict__ hdr, const float4* __restrict__ qnode,
          const float4* __restrict__ chunk_sph, int64_t np, int64_t per_split,
-         double* __restrict__ part, const int32_t* __restrict__ phi_kind)
+         double* __restrict__ part, const int32_t* __restrict__ phi_kind,
+         unsigned long long* __restrict__ chunk_stats)
 {
     constexpr int PC = kPC32;
     constexpr int TR = 2 * TP;
@@ -249,6 +250,7 @@ k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[q][c] = cmp[q][c] = make_float2(0.f, 0.f);
     const float2 eps2 = make_float2(1e-20f, 1e-20f);
+    unsigned n_chunks = 0, n_fast = 0;  // chunk statistics (thread 0)
 
     for (int64_t c0 = p0; c0 < p1; c0 += PC) {
         const int npc = (int)min((int64_t)PC, p1 - c0);
@@ -263,6 +265,8 @@ k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_
         const float4 cs = chunk_sph[c0 / PC];
         const float ddx = cs.x - tc[0], ddy = cs.y - tc[1], ddz = cs.z - tc[2];
         const bool fast = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz) > tr + cs.w;
+        ++n_chunks;
+        n_fast += fast ? 1u : 0u;
         float2 cp[TP][4];
 #pragma unroll
         for (int q = 0; q < TP; ++q)
@@ -397,6 +401,10 @@ k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_
                 }
             }
         }
+    if (tid == 0 && chunk_stats) {
+        atomicAdd(chunk_stats, (unsigned long long)n_chunks);
+        atomicAdd(chunk_stats + 1, (unsigned long long)n_fast);
+    }
 }
 
 template <int TR, int Q, bool RAW>
@@ -673,10 +681,12 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
 #define FAR32P(TP)                                                                                     \
     if (raw)                                                                                           \
         k_far32p<TP, Q, true><<<grid, kThreads, 0, ctx->stream>>>(                                     \
-            nullptr, T.tpts, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part, nullptr); \
+            nullptr, T.tpts, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part, nullptr, \
+            ctx->d_near_count + 2);                                                                    \
     else                                                                                               \
         k_far32p<TP, Q, false><<<grid, kThreads, 0, ctx->stream>>>(                                    \
-            T.t32, nullptr, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part, T.phi_kind)
+            T.t32, nullptr, T.M, ctx->hdr32, ctx->qnode, ctx->chunk_sph, np, per_split, part, T.phi_kind, \
+            ctx->d_near_count + 2)
         if (ctx->far32_tp == 4) {
             FAR32P(4);
         } else {
@@ -743,7 +753,7 @@ int far_splits(const bem_ctx* ctx, int precision, int64_t M)
                                           : (precision == kPrecDF ? kTRdf : kTR64);
     const int pc = precision == BEM_MIXED ? kPC32 : kPC64;
     const int64_t tiles = (M + kThreads * tr - 1) / (kThreads * tr);
-    const int64_t slots = (int64_t)std::max(ctx->num_sms, 1) * 4;
+    const int64_t slots = (int64_t)std::max(ctx->num_sms, 1) * (precision == BEM_MIXED ? ctx->far_slots : 4);
     int64_t s = tiles >= slots ? 1 : slots / std::max<int64_t>(tiles, 1);
     s = std::min<int64_t>(s, std::max<int64_t>(1, ctx->np / (2 * pc)));
     s = std::max<int64_t>(1, std::min<int64_t>(s, 64));

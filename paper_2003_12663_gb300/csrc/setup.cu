@@ -6,7 +6,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "bem_internal.cuh"
 
@@ -382,6 +385,7 @@ static int dalloc(bem_ctx* ctx, T** p, size_t n)
 static void free_ctx(bem_ctx* c)
 {
     if (!c) return;
+    adjoint_workspace_free(c);
     void* ptrs[] = {c->X, c->tri, c->geo, c->hdr32, c->hdr64, c->node32, c->node64, c->tgt32,
                     c->tgt64, c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, c->region_V0,
                     c->row_s, c->float_rows, c->float_off, c->jinv, c->near_ptr, c->near_col, c->near_val,
@@ -437,11 +441,13 @@ extern "C" int bem_get_counters(bem_ctx* c, bem_counters* out)
     if (!c || !out) return BEM_ERR_ARG;
     timing_drain(c);
     BEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    unsigned long long nc[2] = {0, 0};
+    unsigned long long nc[4] = {0, 0, 0, 0};
     BEM_CUDA_TRY(c, cudaMemcpy(nc, c->d_near_count, sizeof nc, cudaMemcpyDeviceToHost));
     *out = c->cnt;
     out->near_pairs[0] += (int64_t)nc[0];
     out->near_pairs[1] += (int64_t)nc[1];
+    out->chunks32p = (int64_t)nc[2];
+    out->fast_chunks32p = (int64_t)nc[3];
     return BEM_OK;
 }
 
@@ -451,7 +457,7 @@ extern "C" int bem_reset_counters(bem_ctx* c)
     timing_drain(c);
     c->cnt = bem_counters{};
     c->cnt.far32_variant = c->far32_tp;
-    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 2 * sizeof(unsigned long long), c->stream));
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 4 * sizeof(unsigned long long), c->stream));
     BEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return BEM_OK;
 }
@@ -468,6 +474,8 @@ extern "C" void bem_default_params(bem_params* p)
     p->max_points = 131072;
     p->timing = 0;
     p->residual = BEM_RESIDUAL_DF;
+    p->adjoint_checkpoint = 128;
+    p->adjoint_lines = 256;
 }
 
 extern "C" const char* bem_last_error(const bem_ctx* ctx)
@@ -507,53 +515,119 @@ extern "C" int bem_destroy(bem_ctx* ctx)
     return BEM_OK;
 }
 
-// The FP32 kernel variant (scalar, 2 or 4 packed target pairs per thread):
-// fixed by params.far32_variant, or picked by timing each candidate on two
-// matvecs of this mesh (CUDA events on the context's stream).  The work counters
-// are cleared afterwards.
+// Tuner of the FP32 regular-pair kernel's shape: the variant (scalar, 2 or 4 packed
+// target pairs per thread) and the CTA slots per SM that the triangle-slice count
+// aims at.  Each candidate is timed on the mesh's own mixed matvec (one warm-up, then
+// CUDA events on the context's stream) and the fastest is kept.  The choice is kept
+// in a process-wide table keyed by (device, size bucket floor(2 log2 N), far_order); later
+// contexts of the same device and bucket take it from there without timing.
+// params.far32_variant != 0 fixes the variant (slots 4); meshes below 4,096
+// triangles take (2, 4) untimed.  The work counters are cleared afterwards.
+namespace {
+struct TuneChoice {
+    int tp, slots;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TuneChoice> g_tune_table;  // (device, bucket, g)
+}  // namespace
+
 static int tune_far32(bem_ctx* c)
 {
+    const int bucket = (int)std::floor(2.0 * std::log2((double)std::max<int64_t>(c->np, 1)));
+    bem_tuning& T = c->tune;
+    T = bem_tuning{};
+    T.bucket = bucket;
     if (c->prm.far32_variant != 0) {
         c->far32_tp = c->prm.far32_variant;
-    } else if (c->np >= 4096) {
-        cudaStream_t s = c->stream;
-        cudaEvent_t e0, e1;
-        BEM_CUDA_TRY(c, cudaEventCreate(&e0));
-        BEM_CUDA_TRY(c, cudaEventCreate(&e1));
-        std::vector<double> ones(c->nunk, 1.0);
-        BEM_CUDA_TRY(c, cudaMemcpyAsync(c->zvec, ones.data(), c->nunk * sizeof(double), cudaMemcpyHostToDevice, s));
-        float best = 3e38f;
-        int best_tp = 2;
-        for (int tp : {1, 2, 4}) {
-            c->far32_tp = tp;
-            int rc = matvec_impl(c, BEM_MIXED, 1, c->zvec, c->wvec);  // warm-up
-            if (!rc) {
-                cudaEventRecord(e0, s);
-                rc = matvec_impl(c, BEM_MIXED, 1, c->zvec, c->wvec);
-                cudaEventRecord(e1, s);
-            }
-            float ms = 3e38f;
-            if (!rc && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-            if (rc) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return rc;
-            }
-            if (ms < best) { best = ms; best_tp = tp; }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        c->far32_tp = best_tp;
-    } else {
+        c->far_slots = 4;
+        T.source = 0;
+    } else if (c->np < 4096) {
         c->far32_tp = 2;
+        c->far_slots = 4;
+        T.source = 0;
+    } else {
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_table.find(std::make_tuple(c->device, bucket, c->g));
+            if (it != g_tune_table.end()) {
+                c->far32_tp = it->second.tp;
+                c->far_slots = it->second.slots;
+                cached = true;
+            }
+        }
+        if (cached) {
+            T.source = 2;
+        } else {
+            cudaStream_t s = c->stream;
+            cudaEvent_t e0, e1;
+            BEM_CUDA_TRY(c, cudaEventCreate(&e0));
+            BEM_CUDA_TRY(c, cudaEventCreate(&e1));
+            std::vector<double> ones(c->nunk, 1.0);
+            BEM_CUDA_TRY(c, cudaMemcpyAsync(c->zvec, ones.data(), c->nunk * sizeof(double),
+                                            cudaMemcpyHostToDevice, s));
+            float best = 3e38f;
+            TuneChoice pick{2, 4};
+            int k = 0;
+            for (int tp : {1, 2, 4}) {
+                for (int sl : {2, 4, 8}) {
+                    c->far32_tp = tp;
+                    c->far_slots = sl;
+                    int rc = matvec_impl(c, BEM_MIXED, 1, c->zvec, c->wvec);  // warm-up
+                    if (!rc) {
+                        cudaEventRecord(e0, s);
+                        rc = matvec_impl(c, BEM_MIXED, 1, c->zvec, c->wvec);
+                        cudaEventRecord(e1, s);
+                    }
+                    float ms = 3e38f;
+                    if (!rc && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                    if (rc) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return rc;
+                    }
+                    T.cand_variant[k] = tp;
+                    T.cand_slots[k] = sl;
+                    T.cand_ms[k] = ms;
+                    ++k;
+                    if (ms < best) {
+                        best = ms;
+                        pick = {tp, sl};
+                    }
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            T.n_candidates = k;
+            T.source = 1;
+            c->far32_tp = pick.tp;
+            c->far_slots = pick.slots;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_table[std::make_tuple(c->device, bucket, c->g)] = pick;
+        }
     }
+    T.far32_variant = c->far32_tp;
+    T.far32_slots = c->far_slots;
     timing_drain(c);
     c->phi_tile_targets = far_phi_tile_targets(c);
     c->cnt = bem_counters{};
     c->cnt.far32_variant = c->far32_tp;
-    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 2 * sizeof(unsigned long long), c->stream));
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 4 * sizeof(unsigned long long), c->stream));
     BEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return BEM_OK;
+}
+
+extern "C" int bem_get_tuning(const bem_ctx* c, bem_tuning* out)
+{
+    if (!c || !out) return BEM_ERR_ARG;
+    *out = c->tune;
+    return BEM_OK;
+}
+
+extern "C" void bem_clear_tuning_table(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_table.clear();
 }
 
 static int create_impl(bem_ctx* c, const bem_mesh* mesh)
@@ -634,8 +708,8 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
             c->nnz_prec[kPrecDF] += (f & 1) ? 1 : 0;  // masked like FP32
         }
     }
-    if ((rc = dalloc(c, &c->d_near_count, 2))) return rc;
-    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 2 * sizeof(unsigned long long), s));
+    if ((rc = dalloc(c, &c->d_near_count, 4))) return rc;
+    BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_near_count, 0, 4 * sizeof(unsigned long long), s));
     if (c->prm.timing) {
         const int pool = 1024;
         c->ev0.resize(pool);
@@ -738,17 +812,21 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     // workspace: far partials for the largest launch
     const int64_t Mmax = std::max<int64_t>(np, c->prm.max_points);
     size_t need = 0;
-    const int tp_default = c->far32_tp;
-    for (int tp : {1, 2, 4}) {  // every FP32 kernel variant the tuner may pick
-        c->far32_tp = tp;
-        for (int prec = 0; prec < 3; ++prec) {
-            for (int64_t M : {np, (int64_t)c->prm.max_points}) {
-                const size_t n = (size_t)far_splits(c, prec, M) * (size_t)M * 4 * kMaxRhs;
-                need = std::max(need, n);
+    const int tp_default = c->far32_tp, slots_default = c->far_slots;
+    for (int tp : {1, 2, 4}) {  // every FP32 kernel shape the tuner may pick
+        for (int sl : {2, 4, 8}) {
+            c->far32_tp = tp;
+            c->far_slots = sl;
+            for (int prec = 0; prec < 3; ++prec) {
+                for (int64_t M : {np, (int64_t)c->prm.max_points}) {
+                    const size_t n = (size_t)far_splits(c, prec, M) * (size_t)M * 4 * kMaxRhs;
+                    need = std::max(need, n);
+                }
             }
         }
     }
     c->far32_tp = tp_default;
+    c->far_slots = slots_default;
     (void)Mmax;
     c->part_cap = need;
     c->m = c->prm.gmres_restart;
@@ -768,6 +846,7 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     }
     BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
     if ((rc = tune_far32(c))) return rc;
+    if ((rc = adjoint_workspace_create(c))) return rc;
     return BEM_OK;
 }
 
@@ -787,6 +866,7 @@ extern "C" int bem_create(bem_ctx** out, const bem_mesh* mesh, const bem_params*
         bem_default_params(&prm);
     if (!(prm.eta >= 1.0) || prm.far_order < 1 || prm.far_order > kMaxOrder ||
         prm.gmres_restart < 1 || prm.gmres_restart > 1000 || prm.max_iters < 1 ||
+        prm.adjoint_lines < 0 || prm.adjoint_checkpoint < 1 ||
         prm.max_refine < 1 || prm.max_points < 1 ||
         (prm.residual != BEM_RESIDUAL_DF && prm.residual != BEM_RESIDUAL_FP64) ||
         (prm.far32_variant != 0 && prm.far32_variant != 1 && prm.far32_variant != 2 &&

@@ -12,7 +12,9 @@
 // cannot use the array's name as a device address (in host code it names a host-side
 // stand-in), so the device address is looked up once per device with
 // cudaGetSymbolAddress, on the first call made with that device current, and then
-// passed to the kernels.
+// passed to the kernels.  The cached address belongs to the device's primary context
+// as it was at that first call; a cudaDeviceReset ends that context and leaves the
+// address stale (the header says so).
 #include <mutex>
 
 #include "bem_internal.cuh"

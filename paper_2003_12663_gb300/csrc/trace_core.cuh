@@ -519,39 +519,24 @@ struct NoRec {
     __device__ void sub(int64_t step, int k, double sig, int kind) {}
 };
 
-// Trace one line from seed xs; the 32 lanes of one warp call this with the same
-// arguments while the other warps of the CTA trace their own lines or idle.  The
-// outputs (K, status, steps, end point) are returned to every lane.
+// The steps [step0, step_end) of a line (capped at max_steps) from the state at the
+// start of step0: point x, integral K, branch side, direction s0 and seed region.
+// The field at x is evaluated afresh, as at every step start after an event, so a
+// line resumed from a state recorded at a step start continues bit for bit as the
+// uninterrupted line (a line's arithmetic does not depend on the lines sharing its
+// rounds).  Status 3 (step limit) is returned when step_end is reached; the caller
+// that resumes knows whether that was a segment's end or the line's.
 template <bool F32, int Q, class Rec>
-__device__ void trace_line(const TArgs& A, Round& R, const double* xs, Rec& rec, double& K_out,
-                           int& st_out, int64_t& ns_out, double* xe_out)
+__device__ void trace_steps(const TArgs& A, Round& R, double* x, double& K, int side, double s0,
+                            int seed_region, int64_t step0, int64_t step_end, Rec& rec, int& st_out,
+                            int64_t& ns_out)
 {
-    double x[3] = {xs[0], xs[1], xs[2]};
-    double K = 0.0;
-    // electrode of the seed: the triangle with the nearest centroid (first on ties)
-    double bd = 1e300;
-    long long bj = 0;
-    for (int64_t j = threadIdx.x & 31; j < A.np; j += 32) {
-        const double* c = A.geo + GEO_STRIDE * j + GEO_CTR;
-        const double dd = (x[0] - c[0]) * (x[0] - c[0]) + (x[1] - c[1]) * (x[1] - c[1]) + (x[2] - c[2]) * (x[2] - c[2]);
-        if (dd < bd) { bd = dd; bj = j; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
-        const long long oj = __shfl_xor_sync(0xffffffffu, bj, o);
-        if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
-    }
-    const int seed_region = A.region[bj];
-    const double* nb = A.geo + GEO_STRIDE * bj + GEO_N;
-    V4 E = field<F32, Q>(A, R, x, -2);
-    const double s0 = (E.x * nb[0] + E.y * nb[1] + E.z * nb[2]) >= 0.0 ? 1.0 : -1.0;
-    int side = norm3(E.x, E.y, E.z) > A.E0 ? 1 : -1;
-    rec.begin(s0, seed_region);
+    V4 E;
     int st = 3;
-    int64_t step = 0;
+    int64_t step = step0;
     bool have = false;  // E holds the field at x (with the seed's indicator)
-    for (; step < A.max_steps; ++step) {
+    const int64_t last = min(step_end, A.max_steps);
+    for (; step < last; ++step) {
         if (!have) E = field<F32, Q>(A, R, x, seed_region);
         have = false;
         const double Em = norm3(E.x, E.y, E.z);
@@ -610,6 +595,42 @@ __device__ void trace_line(const TArgs& A, Round& R, const double* xs, Rec& rec,
         }
         if (done) break;
     }
+    st_out = st;
+    ns_out = step;
+}
+
+// Trace one line from seed xs; the 32 lanes of one warp call this with the same
+// arguments while the other warps of the CTA trace their own lines or idle.  The
+// outputs (K, status, steps, end point) are returned to every lane.
+template <bool F32, int Q, class Rec>
+__device__ void trace_line(const TArgs& A, Round& R, const double* xs, Rec& rec, double& K_out,
+                           int& st_out, int64_t& ns_out, double* xe_out)
+{
+    double x[3] = {xs[0], xs[1], xs[2]};
+    double K = 0.0;
+    // electrode of the seed: the triangle with the nearest centroid (first on ties)
+    double bd = 1e300;
+    long long bj = 0;
+    for (int64_t j = threadIdx.x & 31; j < A.np; j += 32) {
+        const double* c = A.geo + GEO_STRIDE * j + GEO_CTR;
+        const double dd = (x[0] - c[0]) * (x[0] - c[0]) + (x[1] - c[1]) * (x[1] - c[1]) + (x[2] - c[2]) * (x[2] - c[2]);
+        if (dd < bd) { bd = dd; bj = j; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const long long oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
+    }
+    const int seed_region = A.region[bj];
+    const double* nb = A.geo + GEO_STRIDE * bj + GEO_N;
+    V4 E = field<F32, Q>(A, R, x, -2);
+    const double s0 = (E.x * nb[0] + E.y * nb[1] + E.z * nb[2]) >= 0.0 ? 1.0 : -1.0;
+    int side = norm3(E.x, E.y, E.z) > A.E0 ? 1 : -1;
+    rec.begin(s0, seed_region);
+    int st;
+    int64_t step;
+    trace_steps<F32, Q>(A, R, x, K, side, s0, seed_region, 0, A.max_steps, rec, st, step);
     K_out = K;
     st_out = st;
     ns_out = step;

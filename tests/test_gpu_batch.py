@@ -266,3 +266,39 @@ def test_batch_device_family_sampled(bem):
     B.close()
     for c in ctxs:
         c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (0, 1e-11)], ids=["mixed", "fp64"])
+def test_batch_eval_field_vs_oracle(fam, bem, prec, tol):
+    """bem_batch_eval_field: every instance's points (uneven counts, one instance with
+    none, ragged tiles, points 1e-4 off the surface) against the oracle's field, and
+    (mixed) against each instance's own bem_eval_field."""
+    meshes, ctxs, probs, mats = fam
+    B = bem.Batch(ctxs, nrhs=1)
+    rng = np.random.default_rng(17)
+    us, pts = [], []
+    for k, (m, P, A) in enumerate(zip(meshes, probs, mats)):
+        us.append(torch.tensor(1.0 + 0.2 * rng.standard_normal(P.N + P.F)))
+        if k == 1:
+            pts.append(np.zeros((0, 3)))
+            continue
+        n_box = [300, 0, 1234, 517][k]
+        pts.append(np.concatenate([mg.device_box_points(n_box, seed=30 + k),
+                                   P.centroids[::23] + 1e-4 * P.normals[::23]]))
+    B.reset_counters()
+    phi, E = B.eval_field(us, pts, precision=prec)
+    torch.cuda.synchronize()
+    for k, P in enumerate(probs):
+        if len(pts[k]) == 0:
+            assert phi[k].numel() == 0
+            continue
+        pr, Er = P.field(us[k].numpy(), pts[k])
+        assert np.abs(phi[k].cpu().numpy() - pr).max() <= tol * np.abs(pr).max()
+        assert np.abs(E[k].cpu().numpy() - Er).max() <= tol * np.abs(Er).max()
+        if prec == bem.MIXED:
+            p1, E1 = ctxs[k].eval_field(us[k], torch.tensor(pts[k]), bem.MIXED)
+            assert (E[k] - E1).abs().max().item() <= 1e-5 * E1.abs().max().item()
+    if prec == bem.MIXED:
+        c = B.counters()
+        assert c["eval_pairs"] == sum(len(p) * P.N for p, P in zip(pts, probs))
+    B.close()

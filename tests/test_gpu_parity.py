@@ -200,3 +200,61 @@ def test_rhs_and_multi_rhs(case, bem):
     u, iters, rel = ctx.solve(0, V0=torch.tensor(V0), tol=1e-11, nrhs=2)
     u = u.cpu().numpy()
     assert np.allclose(u[1], -2.0 * u[0], rtol=1e-8, atol=1e-10 * np.abs(u[0]).max())
+
+
+# ------------------------------------------------------------ FP32 kernel variants
+# The context's tuner picks the FP32 regular-pair kernel (scalar k_far32, packed
+# k_far32p with 2 or 4 target pairs per thread) only on meshes of 4,096 triangles or
+# more; below that it fixes the 2-pair variant.  Every variant is compared with the
+# oracle here, on every mesh above, by fixing it through bem_params.far32_variant.
+@pytest.fixture(scope="module", params=[1, 2, 4], ids=lambda v: f"far32v{v}")
+def variant_case(request, case, bem):
+    name, mesh, ctx, P, A = case
+    c = bem.Context(mesh, far32_variant=request.param)
+    assert c.counters()["far32_variant"] == request.param
+    yield request.param, name, mesh, c, P, A
+    c.close()
+
+
+def test_variant_rows_mixed(variant_case, bem):
+    v, name, mesh, ctx, P, A = variant_case
+    G = ctx.assemble_rows(precision=bem.MIXED).cpu().numpy()
+    assert _rel_rows(G, A) < 2e-6
+
+
+def test_variant_matvec_mixed(variant_case, bem):
+    v, name, mesh, ctx, P, A = variant_case
+    x = np.random.default_rng(13).normal(size=(2, ctx.nunk))
+    ctx.reset_counters()
+    y = ctx.matvec(torch.tensor(x), precision=bem.MIXED).cpu().numpy()
+    ref = x @ A.T
+    err = np.abs(y - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    assert err.max() < 2e-6, err
+    c = ctx.counters()
+    if v > 1:
+        assert c["chunks32p"] > 0   # the packed kernel ran
+    else:
+        assert c["chunks32p"] == 0  # the scalar kernel ran
+
+
+def test_variant_eval_field_mixed(variant_case, bem):
+    v, name, mesh, ctx, P, A = variant_case
+    u_ref = np.linalg.solve(A, P.rhs())
+    if name == "sphere_l3":
+        pts = np.concatenate([mg.sphere_eval_points(1, 700, 700), P.centroids[::9] * (1 + 1e-4)])
+    else:
+        pts = np.concatenate([mg.device_box_points(1400, 5), P.centroids[::17] + 1e-4 * P.normals[::17]])
+    pts = pts[: len(pts) - 3]
+    phi_r, E_r = P.field(u_ref, pts)
+    phi, E = ctx.eval_field(torch.tensor(u_ref), torch.tensor(pts), precision=bem.MIXED)
+    phi, E = phi.cpu().numpy(), E.cpu().numpy()
+    assert np.abs(phi - phi_r).max() / np.abs(phi_r).max() < 1e-5
+    assert np.abs(E - E_r).max() / np.abs(E_r).max() < 1e-5
+
+
+def test_variant_solve_mixed(variant_case, bem):
+    v, name, mesh, ctx, P, A = variant_case
+    u_ref = np.linalg.solve(A, P.rhs())
+    u, iters, rel = ctx.solve(bem.MIXED, tol=1e-10)
+    u = u[0].cpu().numpy()
+    assert np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) < 1e-6

@@ -53,3 +53,22 @@ def test_static_scratch_limits(setup):
     assert ei.value.code == -7 and "65536" in str(ei.value)
     phi, E = ctx.eval_field_static(u, torch.zeros((0, 3), dtype=torch.float64))
     assert phi.numel() == 0
+
+
+def test_static_call_allocates_nothing(setup):
+    """With phi and E passed in, a call changes neither torch's allocator nor the
+    device's free memory (after a first call, which may load the kernels' module)."""
+    bem, ctx, u = setup
+    pts = torch.tensor(mg.device_box_points(4096, seed=8), device="cuda")
+    phi = torch.empty(4096, dtype=torch.float64, device="cuda")
+    E = torch.empty((4096, 3), dtype=torch.float64, device="cuda")
+    ctx.eval_field_static(u, pts, bem.MIXED, phi=phi, E=E)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.memory_allocated()
+    f0, _ = torch.cuda.mem_get_info()
+    for prec in (bem.MIXED, bem.FP64):
+        ctx.eval_field_static(u, pts, prec, phi=phi, E=E)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == a0
+    f1, _ = torch.cuda.mem_get_info()
+    assert f1 == f0
