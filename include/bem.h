@@ -377,6 +377,57 @@ int bem_surface_field(bem_ctx* ctx, int32_t precision, const double* u_dev, doub
  */
 int bem_measure_peaks(double* fp32_tflops, double* fp64_tflops, double* fp32_scalar_tflops);
 
+/* ------------------------------------------------------------------ curved triangles
+ * The paper's own discretisation (Sec. 3, Sec. 4): six-node triangles (corners, then
+ * the midpoints of the edges 01, 12, 20, which may lie off the corners' plane: a
+ * piecewise quadratic surface), the density sigma_h = sum_v u_v psi_v with psi_v the
+ * mapped linear function that is 1 at vertex v, collocation at the vertices:
+ *     v_ij = sum_T int psi_j(y) / (4 pi |x_i - y|) dS_y        (Eq. Matrix).
+ * Pairs (vertex, triangle) are singular when the vertex is a corner of the
+ * triangle (Duffy rule collapsed there, sing_order^2 points), regular when D > eta R
+ * with the circumcircle of the corners (Duffy rule collapsed at corner 0, far_order^2
+ * Gauss-Legendre points), near-singular otherwise (split at the point of the curved
+ * triangle closest to the vertex, found by projected Gauss-Newton; each part a Duffy
+ * rule collapsed there with near_radial points per geometric radial piece, refined
+ * toward it down to a tenth of distance / size, and near_angular angular points).
+ * Rows: conductor vertices sum_j v_ij u_j = V0 (Eq. Final1), floating vertices
+ * sum_j v_ij u_j - V_f = 0 (Eq. Final2), one neutrality row per floating body in the
+ * form Gauss's law gives a closed conductor, int_body sigma_h dS = 0 (Eq. Final4).
+ * Dielectric and sheet regions are not built on this path.
+ * The context this creates serves bem_destroy, bem_sizes, bem_get_counters,
+ * bem_assemble_rows, bem_matvec (BEM_FP64, BEM_MIXED), bem_rhs, bem_solve (the
+ * mixed form refines with the FP64 product) and bem_eval_field; the other calls
+ * return BEM_ERR_ARG.  Unknowns: u at the vertices 0..nv-1, then V_f.
+ */
+typedef struct {
+    double eta;              /* regular iff D > eta R; default 4 */
+    int32_t far_order;       /* regular rule far_order x far_order points, 1..6; default 4 */
+    int32_t sing_order;      /* singular rule sing_order x sing_order; default 24 */
+    int32_t near_radial;     /* near-singular rule: points per radial piece; default 16 */
+    int32_t near_angular;    /* near-singular rule: angular points; default 64 */
+    int32_t gmres_restart, max_iters, max_refine;  /* as bem_params: 100, 2000, 6 */
+    int32_t far32_variant;   /* packed FP32 kernel, 2 or 4 target pairs per thread; default 2 */
+    int64_t max_points;      /* as bem_params; default 131072 */
+    int32_t timing;          /* as bem_params */
+    int32_t reserved;
+} bem_p1_params;
+
+void bem_p1_default_params(bem_p1_params* p);
+
+/*
+ * Create a context of curved six-node triangles.  nodes: host double [nn][3], the
+ * first nv of them the triangle corners (vertices, the collocation points); tri6:
+ * host int32 [N][6] node indices (corners counter-clockwise about the outward
+ * normal, then edge midpoints 01, 12, 20); region: host int32 [N]; regions: host
+ * [nregions], conductor or floating kinds only (every vertex's triangles must share
+ * its region).  Set-up computes every singular and near-singular integral in FP64 on
+ * the device.  Errors: BEM_ERR_ARG, BEM_ERR_DEGENERATE (collinear corners),
+ * BEM_ERR_NOMEM, BEM_ERR_CUDA; on error *out is NULL.
+ */
+int bem_p1_create(bem_ctx** out, int64_t nn, const double* nodes, int64_t nv, int64_t N, const int32_t* tri6,
+                  const int32_t* region, int32_t nregions, const bem_region* regions,
+                  const bem_p1_params* params, void* stream);
+
 /* ------------------------------------------------------------------ batches
  * Many meshes (instances) of uneven size with up to four right-hand sides each,
  * served together: the operators are those of bem_matvec / bem_solve /

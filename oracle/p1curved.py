@@ -352,7 +352,13 @@ class CurvedProblem:
         return out
 
     def solve(self, regions, body, V0_scale: float = 1.0):
-        """Unknowns (u at the vertices, then V_f of each floating body) for regions
+        """Unknowns (u at the vertices, then V_f of each floating body) and the
+        vertices' regions: the system of system() solved by LU (numpy/LAPACK)."""
+        A, b, vreg = self.system(regions, body, V0_scale)
+        return np.linalg.solve(A, b), vreg
+
+    def system(self, regions, body, V0_scale: float = 1.0):
+        """The collocation system (A, b, vreg) for regions
         (dicts, as for flat meshes) given per triangle by body:
           conductor rows  sum_j v_ij u_j = V0                      (Eq. Final1)
           floating rows   sum_j v_ij u_j - V_f = 0                  (Eq. Final2)
@@ -360,7 +366,7 @@ class CurvedProblem:
           neutrality      int_{body f} sigma_h dS = 0               (Eq. Final4)
         The neutrality row uses Gauss's law on a closed conductor (no field inside):
         int eps+ (sigma/2 + K'sigma) dS = eps+ int E+.n dS = eps+ int sigma dS.
-        A vertex takes the region of its triangles.  Returns (x, vreg)."""
+        A vertex takes the region of its triangles."""
         vreg = np.full(self.nv, -1)
         for T in range(self.N):
             for v in self.tri6[T, :3]:
@@ -398,7 +404,7 @@ class CurvedProblem:
                 ep, em = regions[vreg[i]]["eps_plus"], regions[vreg[i]]["eps_minus"]
                 A[i] = (ep - em) * K[k]
                 A[i, i] += 0.5 * (ep + em)
-        return np.linalg.solve(A, b), vreg
+        return A, b, vreg
 
     def integrate(self, u=None):
         """int sigma_h dS (the total charge) for vertex values u, or the area if

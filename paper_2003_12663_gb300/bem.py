@@ -91,6 +91,14 @@ class bem_tuning(ctypes.Structure):
                                 "ms": self.cand_ms[k]} for k in range(n)]}
 
 
+class bem_p1_params(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("far_order", ctypes.c_int32), ("sing_order", ctypes.c_int32),
+                ("near_radial", ctypes.c_int32), ("near_angular", ctypes.c_int32),
+                ("gmres_restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("far32_variant", ctypes.c_int32),
+                ("max_points", ctypes.c_int64), ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class bem_batch_counters(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_int64), ("nrhs", ctypes.c_int64),
                 ("far_launches", ctypes.c_int64), ("pairs", ctypes.c_int64),
@@ -130,6 +138,9 @@ _SIGS = {
     "bem_trace_lines": (_i32, [_vp, _i32, _vp, _i64, _vp, ctypes.POINTER(bem_trace_params), _vp,
                                _vp, _vp, _vp]),
     "bem_measure_peaks": (_i32, [ctypes.POINTER(_dbl)] * 3),
+    "bem_p1_default_params": (None, [ctypes.POINTER(bem_p1_params)]),
+    "bem_p1_create": (_i32, [ctypes.POINTER(_vp), _i64, _vp, _i64, _i64, _vp, _vp, _i32,
+                             ctypes.POINTER(bem_region), ctypes.POINTER(bem_p1_params), _vp]),
     "bem_get_tuning": (_i32, [_vp, ctypes.POINTER(bem_tuning)]),
     "bem_clear_tuning_table": (None, []),
     "bem_batch_create": (_i32, [_pvp, _pvp, _i32, _i32, _i32]),
@@ -387,6 +398,56 @@ def measure_peaks() -> dict:
     a, b, c = _dbl(), _dbl(), _dbl()
     _check(lib().bem_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), None)
     return {"fp32_tflops": a.value, "fp64_tflops": b.value, "fp32_scalar_tflops": c.value}
+
+
+def _regions(regions):
+    regs = (bem_region * len(regions))()
+    for k, r in enumerate(regions):
+        regs[k].kind = _KIND[r["kind"]]
+        regs[k].floating_id = int(r.get("floating_id", 0))
+        regs[k].V0 = float(r.get("V0", 0.0))
+        regs[k].eps_plus = float(r.get("eps_plus", 1.0))
+        regs[k].eps_minus = float(r.get("eps_minus", 1.0))
+    return regs
+
+
+class P1Context(Context):
+    """Curved six-node triangles with the mapped linear basis, collocation at the
+    vertices (bem_p1_create).  nodes [nn, 3] (the first nv the corners), tri6 [N, 6],
+    body [N] region index per triangle, regions as for flat meshes (conductor and
+    floating kinds).  Products, solves, dense rows and fields as Context."""
+
+    def __init__(self, nodes, tri6, nv, body, regions, stream=None, **params):
+        import torch
+        self._torch = torch
+        L = lib()
+        self.nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        self.tri6 = np.ascontiguousarray(tri6, dtype=np.int32)
+        self.body = np.ascontiguousarray(body, dtype=np.int32)
+        self._regs = _regions(regions)
+        p = bem_p1_params()
+        L.bem_p1_default_params(ctypes.byref(p))
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        self.p1params = p
+        self.params = default_params()
+        self.params.eta, self.params.far_order = p.eta, p.far_order
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = L.bem_p1_create(ctypes.byref(h), len(self.nodes), self.nodes.ctypes.data_as(ctypes.c_void_p),
+                             int(nv), len(self.tri6), self.tri6.ctypes.data_as(ctypes.c_void_p),
+                             self.body.ctypes.data_as(ctypes.c_void_p), len(regions), self._regs,
+                             ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream))
+        _check(rc, None)
+        self.h = h
+        a, b, c, d = (ctypes.c_int64() for _ in range(4))
+        _check(L.bem_sizes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), h)
+        self.np, self.nunk, self.nfloat, self.near_pairs = a.value, b.value, c.value, d.value
+        self.nv = int(nv)
+        self.nregions = len(regions)
+        self.X = self.nodes[: self.nv]
 
 
 def _ptr_array(tensors):

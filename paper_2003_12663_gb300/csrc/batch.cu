@@ -776,7 +776,7 @@ extern "C" int bem_batch_create(bem_batch** out, bem_ctx* const* ctxs, int32_t n
     if (!ctxs || n < 1 || nrhs < 1 || nrhs > kMaxRhs) return BEM_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         const bem_ctx* c = ctxs[i];
-        if (!c || c->device != ctxs[0]->device || c->stream != ctxs[0]->stream || c->g != ctxs[0]->g ||
+        if (!c || c->p1 || c->device != ctxs[0]->device || c->stream != ctxs[0]->stream || c->g != ctxs[0]->g ||
             c->m != ctxs[0]->m || c->g < 2 || c->g > 4)
             return BEM_ERR_ARG;  // one device, one stream, one far_order in 2..4, one restart length
     }

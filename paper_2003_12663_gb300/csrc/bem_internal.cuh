@@ -29,6 +29,7 @@ constexpr int kPrecDF = BEM_DF;       // regular pairs in double-FP32 arithmetic
 constexpr double kInv4Pi = 0.07957747154594767;  // 1/(4 pi)
 
 struct AdjWork;  // adjoint.cu: the workspace of bem_adjoint
+struct P1Data;   // p1.cu: a context of curved six-node triangles with P1 densities
 
 struct bem_ctx {
     cudaStream_t stream = nullptr;
@@ -121,9 +122,25 @@ struct bem_ctx {
     size_t ev_used = 0;
 
     AdjWork* adj = nullptr;        // adjoint workspace (params.adjoint_lines > 0)
+    // curved-triangle (P1) context: the regular-pair kernels take the density folded
+    // into qnode / qnode64 per product, with a unit factor per triangle (ones)
+    P1Data* p1 = nullptr;
+    double4* qnode64 = nullptr;
+    const double* ones = nullptr;
 
     std::string err;
 };
+
+// p1.cu: the curved-triangle path behind the generic calls
+int p1_matvec_impl(bem_ctx* ctx, int precision, int nrhs, const double* x, double* y);
+int p1_rhs(bem_ctx* ctx, int nrhs, const double* V0, double* b);
+int p1_eval_field(bem_ctx* ctx, int precision, const double* u, int64_t M, const double* pts, double* phi,
+                  double* E);
+int p1_assemble(bem_ctx* ctx, int64_t row0, int64_t row1, int precision, double* A, int64_t lda);
+void p1_free(bem_ctx* ctx);
+// setup.cu: n-point Gauss-Legendre rule on [-1, 1]; bounding spheres of 32-triangle chunks
+void gauss_legendre_pm1(int n, std::vector<double>& x, std::vector<double>& w);
+__global__ void k_chunk_spheres(int64_t np, const double* __restrict__ geo, float4* __restrict__ sph);
 
 // adjoint.cu: the adjoint workspace, allocated by bem_create and freed with the context
 int adjoint_workspace_create(bem_ctx* ctx);

@@ -672,10 +672,14 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
     // slices start on whole 32-triangle chunks (the chunk spheres of k_far32p)
     const int64_t per_split = ((np + splits - 1) / splits + kPC32 - 1) / kPC32 * kPC32;
     const bool raw = (T.tpts != nullptr);
+    if (ctx->p1 && (precision == kPrecDF || (precision == BEM_MIXED && ctx->far32_tp < 2)))
+        return set_err(ctx, BEM_ERR_ARG, "curved triangles: packed FP32 or FP64 regular pairs only");
     if (precision == BEM_MIXED && ctx->far32_tp > 1) {
-        const int64_t n = np * Q;
-        k_prescale<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, Q, ctx->node32, u, ctx->qnode);
-        BEM_LAUNCH_CHECK(ctx);
+        if (!ctx->p1) {  // a curved-triangle context folds its density itself
+            const int64_t n = np * Q;
+            k_prescale<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, Q, ctx->node32, u, ctx->qnode);
+            BEM_LAUNCH_CHECK(ctx);
+        }
         const int tr = 2 * ctx->far32_tp;
         dim3 grid((unsigned)((T.M + kThreads * tr - 1) / (kThreads * tr)), (unsigned)splits);
 #define FAR32P(TP)                                                                                     \
@@ -707,13 +711,15 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
             k_far32<kTR32, Q, false><<<grid, kThreads, 0, ctx->stream>>>(
                 T.t32, nullptr, T.M, ctx->hdr32, ctx->node32, u, np, per_split, part);
     } else {
+        // a curved-triangle context passes its folded nodes with a unit density
+        const double4* nodes = ctx->p1 ? ctx->qnode64 : ctx->node64;
         dim3 grid((unsigned)((T.M + kThreads * kTR64 - 1) / (kThreads * kTR64)), (unsigned)splits);
         if (raw)
             k_far64<kTR64, Q, true><<<grid, kThreads, 0, ctx->stream>>>(
-                nullptr, T.tpts, T.M, ctx->hdr64, ctx->node64, u, np, per_split, part);
+                nullptr, T.tpts, T.M, ctx->hdr64, nodes, u, np, per_split, part);
         else
             k_far64<kTR64, Q, false><<<grid, kThreads, 0, ctx->stream>>>(
-                T.t64, nullptr, T.M, ctx->hdr64, ctx->node64, u, np, per_split, part);
+                T.t64, nullptr, T.M, ctx->hdr64, nodes, u, np, per_split, part);
     }
     BEM_LAUNCH_CHECK(ctx);
     return BEM_OK;

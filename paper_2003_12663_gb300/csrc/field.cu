@@ -388,6 +388,7 @@ int assemble_dispatch(bem_ctx* c, int64_t row0, int64_t row1, double* A, int64_t
 
 int matvec_impl(bem_ctx* c, int precision, int nrhs, const double* x, double* y, bool need_E)
 {
+    if (c->p1) return p1_matvec_impl(c, precision, nrhs, x, y);
     const int64_t np = c->np, n = c->nunk;
     const int splits = far_splits(c, precision, np);
     if ((size_t)splits * np * 4 * nrhs > c->part_cap)
@@ -430,6 +431,8 @@ extern "C" int bem_matvec(bem_ctx* c, int32_t precision, int32_t nrhs, const dou
         if (int rc = check_prec(c, precision)) return rc;
     if (nrhs < 1 || nrhs > kMaxRhs || !x || !y)
         return set_err(c, BEM_ERR_ARG, "bem_matvec: need 1 <= nrhs <= %d and non-NULL x, y", kMaxRhs);
+    if (c->p1 && precision == BEM_DF)
+        return set_err(c, BEM_ERR_ARG, "bem_matvec: BEM_DF is not built for curved triangles");
     return matvec_impl(c, precision, nrhs, x, y);
 }
 
@@ -440,6 +443,7 @@ extern "C" int bem_rhs(bem_ctx* c, int32_t nrhs, const double* V0, double* b)
     const int nreg = (int)c->regions.size();
     const double* v = V0 ? V0 : c->region_V0;
     if (!V0 && nrhs != 1) return set_err(c, BEM_ERR_ARG, "bem_rhs: V0 = NULL needs nrhs = 1");
+    if (c->p1) return p1_rhs(c, nrhs, V0, b);
     dim3 grid((unsigned)((c->nunk + 255) / 256), (unsigned)nrhs);
     k_rhs<<<grid, 256, 0, c->stream>>>(c->np, c->nunk, nreg, c->row_kind, c->row_aux, v, b);
     BEM_LAUNCH_CHECK(c);
@@ -451,6 +455,7 @@ extern "C" int bem_surface_field(bem_ctx* c, int32_t precision, const double* u,
     if (!c) return BEM_ERR_ARG;
     if (int rc = check_prec(c, precision)) return rc;
     if (!u || !E) return set_err(c, BEM_ERR_ARG, "bem_surface_field: NULL pointer");
+    if (c->p1) return set_err(c, BEM_ERR_ARG, "bem_surface_field: not built for curved triangles");
     const int64_t np = c->np;
     const int splits = far_splits(c, precision, np);
     FarTargets T{c->tgt32, c->tgt_lo32, c->tgt64, nullptr, np};
@@ -489,6 +494,7 @@ extern "C" int bem_eval_field(bem_ctx* c, int32_t precision, const double* u, in
     if (!c) return BEM_ERR_ARG;
     if (int rc = check_prec(c, precision)) return rc;
     if (M < 0 || (M > 0 && (!u || !pts))) return set_err(c, BEM_ERR_ARG, "bem_eval_field: bad M or NULL");
+    if (c->p1) return M > 0 ? p1_eval_field(c, precision, u, M, pts, phi, E) : BEM_OK;
     const int64_t CH = c->prm.max_points;
     for (int64_t m0 = 0; m0 < M; m0 += CH) {
         const int64_t mc = std::min(CH, M - m0);
@@ -520,6 +526,7 @@ extern "C" int bem_assemble_rows(bem_ctx* c, int64_t row0, int64_t row1, int32_t
     if (row0 < 0 || row1 < row0 || row1 > c->nunk || lda < c->nunk || (!A && row1 > row0))
         return set_err(c, BEM_ERR_ARG, "bem_assemble_rows: bad rows [%lld,%lld) or lda",
                        (long long)row0, (long long)row1);
+    if (c->p1) return p1_assemble(c, row0, row1, precision, A, lda);
     return precision == BEM_MIXED ? assemble_dispatch<true>(c, row0, row1, A, lda)
                                   : assemble_dispatch<false>(c, row0, row1, A, lda);
 }

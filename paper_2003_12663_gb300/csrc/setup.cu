@@ -32,7 +32,7 @@ int set_err(bem_ctx* ctx, int code, const char* fmt, ...)
 // ---------------------------------------------------------------- Gauss rules
 // n-point Gauss-Legendre on [-1,1]: Newton's method on P_n, evaluated by the
 // three-term recurrence (k+1) P_{k+1} = (2k+1) z P_k - k P_{k-1}.
-static void gauss_legendre_pm1(int n, std::vector<double>& x, std::vector<double>& w)
+void gauss_legendre_pm1(int n, std::vector<double>& x, std::vector<double>& w)
 {
     x.assign(n, 0.0);
     w.assign(n, 0.0);
@@ -386,6 +386,7 @@ static void free_ctx(bem_ctx* c)
 {
     if (!c) return;
     adjoint_workspace_free(c);
+    p1_free(c);
     void* ptrs[] = {c->X, c->tri, c->geo, c->hdr32, c->hdr64, c->node32, c->node64, c->tgt32,
                     c->tgt64, c->row_kind, c->row_aux, c->row_a, c->row_b, c->row_w, c->region_V0,
                     c->row_s, c->float_rows, c->float_off, c->jinv, c->near_ptr, c->near_col, c->near_val,

@@ -67,6 +67,7 @@ extern "C" int bem_eval_field_static(bem_ctx* c, int32_t precision, const double
         return set_err(c, BEM_ERR_CAPACITY,
                        "bem_eval_field_static: M = %lld points exceeds the fixed scratch limit of %lld "
                        "points per call", (long long)M, (long long)kMaxPoints);
+    if (c->p1) return set_err(c, BEM_ERR_ARG, "bem_eval_field_static: not built for curved triangles");
     double* scratch = nullptr;
     if (int rc = scratch_address(c, &scratch)) return rc;
     if (M == 0) return BEM_OK;

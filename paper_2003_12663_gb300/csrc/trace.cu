@@ -81,6 +81,7 @@ extern "C" void bem_default_trace_params(bem_trace_params* tp)
 
 int trace_args(bem_ctx* c, const bem_trace_params* tp, const double* u, tcore::TArgs* out)
 {
+    if (c->p1) return set_err(c, BEM_ERR_ARG, "field lines are not built for curved triangles");
     bem_trace_params p;
     if (tp)
         p = *tp;
