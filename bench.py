@@ -62,7 +62,7 @@ def parse():
                     help="matvec: only W+K mixed matvecs of the workload (a small case for ncu); "
                          "batch: the uneven device family solved and traced by the batched calls; "
                          "report: per-configuration times and errors of both GPU forms and the oracle")
-    ap.add_argument("--report-configs", default="c1,c2,c3,bushing,c5", help="report mode: configurations")
+    ap.add_argument("--report-configs", default="c1,c2,c3,bushing,p1,c5", help="report mode: configurations")
     ap.add_argument("--c5-lines", type=int, default=64, help="report mode: field lines traced on c5")
     ap.add_argument("--lines", type=int, default=512, help="trace mode: field lines")
     ap.add_argument("--seed-radius", type=float, default=1.05,
@@ -411,6 +411,7 @@ def run_ours(args):
                 "fp32_far_ms_per_step": far_ms / args.steps}
     if peaks:
         roofline["fp64_peak_tflops_measured"] = peaks["fp64_tflops"]
+    roofline["tuning"] = ctx.tuning()   # the kernel shape bem_create's tuner chose, and the candidates' times
 
     rel = out["rel"][0]
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -925,6 +926,24 @@ def run_report(args):
                          "pairs_per_s": rate, "sample": f"{rows} rows x {mesh.np_} triangles, {secs:.1f} s",
                          "one_product_s_extrapolated": mesh.np_ ** 2 / rate}
         emit(out)
+    if "p1" in want:
+        # the paper's own discretisation: curved six-node triangles, P1 at the vertices
+        for level in (3, 4):
+            nodes, tri6, nv = mg.quadratic_sphere(level)
+            body = np.zeros(len(tri6), np.int32)
+            regs = [{"kind": "conductor", "V0": 1.0}]
+            ctx, t_set = wall(lambda: bem.P1Context(nodes, tri6, nv, body, regs))
+            res = {}
+            for name, prec in (("fp64", bem.FP64), ("mixed", bem.MIXED)):
+                (u, it, rel), t_sol = timed(lambda: ctx.solve(prec, tol=1e-10))
+                x = u[0]
+                _, t_mv = timed(lambda: ctx.matvec(x, prec))
+                res[name] = {"solve_ms": t_sol, "iters": it, "relres": rel[0], "matvec_ms": t_mv,
+                             "max_abs_sigma_minus_1": float((u[0] - 1.0).abs().max().item())}
+            emit({"config": f"curved sphere level {level}: {len(tri6)} six-node triangles, {nv} vertices, "
+                            f"P1 collocation, V0=1, tol 1e-10",
+                  "setup_ms": t_set, "near_pairs": ctx.near_pairs, **res})
+            ctx.close()
     if "c5" in want:
         scale = (200000 / 20068.0) ** 0.5
         mesh = mg.device_mesh(scale, seed=2)

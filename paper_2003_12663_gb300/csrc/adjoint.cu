@@ -1144,6 +1144,7 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     constexpr size_t fsm = field_smem<F32, Q>();
     BEM_CUDA_TRY(c, allow_smem(k_adj_forward<F32, Q>, fsm));
     BEM_CUDA_TRY(c, allow_smem(k_adj_resume<F32, Q>, fsm));
+    const int ncl = tracer_cluster(np);  // the cluster size of bem_trace_lines on this mesh
     BEM_CUDA_TRY(c, cudaMemsetAsync(W.gu, 0, c->nunk * sizeof(double), s));
     BEM_CUDA_TRY(c, cudaMemsetAsync(W.gPt, 0, 9 * np * sizeof(double), s));
     std::vector<int64_t> h_n(chunk);
@@ -1151,10 +1152,10 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     for (int64_t c0 = 0; c0 < L; c0 += chunk) {
         const int64_t nc = std::min(chunk, L - c0);
         // 1. forward: K, status, step-record counts and a checkpoint every k steps
-        const unsigned fgrid = lines_grid(k_adj_forward<F32, Q>, fsm, c->num_sms, nc);
+        const unsigned fgrid = lines_grid(k_adj_forward<F32, Q>, fsm, c->num_sms, nc, ncl);
         BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), s));
-        k_adj_forward<F32, Q><<<fgrid, kLT, fsm, s>>>(A, seeds + 3 * c0, nc, c->d_line_next, W.cp, ncp, k,
-                                                      W.nrec, W.s0, W.sr, W.K, W.st);
+        BEM_CUDA_TRY(c, launch_lines(k_adj_forward<F32, Q>, fgrid, fsm, s, ncl, A, seeds + 3 * c0, nc,
+                                     c->d_line_next, W.cp, ncp, k, W.nrec, W.s0, W.sr, W.K, W.st));
         BEM_LAUNCH_CHECK(c);
         if (K_out) BEM_CUDA_TRY(c, cudaMemcpyAsync(K_out + c0, W.K, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
         BEM_CUDA_TRY(c, cudaMemcpyAsync(h_n.data(), W.nrec, nc * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1173,11 +1174,13 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
             BEM_CUDA_TRY(c, cudaMemsetAsync(W.gul, 0, nb * np * sizeof(double), s));
             BEM_CUDA_TRY(c, cudaMemsetAsync(W.gpl, 0, nb * 9 * np * sizeof(double), s));
             BEM_CUDA_TRY(c, cudaMemsetAsync(W.lx, 0, 3 * nb * sizeof(double), s));
-            const unsigned rgrid = lines_grid(k_adj_resume<F32, Q>, fsm, c->num_sms, nb);
+            const unsigned rgrid = lines_grid(k_adj_resume<F32, Q>, fsm, c->num_sms, nb, ncl);
             for (int64_t seg = segs - 1; seg >= 0; --seg) {
                 BEM_CUDA_TRY(c, cudaMemsetAsync(c->d_line_next, 0, sizeof(unsigned long long), s));
-                k_adj_resume<F32, Q><<<rgrid, kLT, fsm, s>>>(A, nb, c->d_line_next, W.cp + b0 * ncp, ncp, k, seg,
-                                                             W.nrec + b0, W.s0 + b0, W.sr + b0, W.tape, W.segn);
+                BEM_CUDA_TRY(c, launch_lines(k_adj_resume<F32, Q>, rgrid, fsm, s, ncl, A, nb, c->d_line_next,
+                                             (const Ckpt*)(W.cp + b0 * ncp), ncp, k, seg,
+                                             (const int64_t*)(W.nrec + b0), (const double*)(W.s0 + b0),
+                                             (const int*)(W.sr + b0), W.tape, W.segn));
                 BEM_LAUNCH_CHECK(c);
                 k_adj_backward<F32, Q><<<(unsigned)nb, kT, 0, s>>>(A, c->g, W.tape, k, W.segn, W.s0 + b0,
                                                                    wts + c0 + b0, nb, W.gul, W.gpl, W.lx);

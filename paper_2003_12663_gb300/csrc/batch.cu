@@ -1270,14 +1270,19 @@ extern "C" int bem_batch_trace(bem_batch* b, int32_t precision, const double* co
     int32_t* const* d_st = (int32_t* const*)(b->d_tptr + 2 * n);
     int32_t* const* d_ns = (int32_t* const*)(b->d_tptr + 3 * n);
     int rc = BEM_OK;
+    // clusters of two CTAs when any mesh is large enough to be split (a smaller mesh is
+    // still swept by the leader alone, exactly as in its own bem_trace_lines)
+    int64_t npmax = 0;
+    for (int i = 0; i < n; ++i) npmax = std::max(npmax, b->ctx[i]->np);
+    const int ncl = tcore::tracer_cluster(npmax);
     switch (b->g * 2 + (precision == BEM_MIXED ? 1 : 0)) {
 #define BT(G, QQ, F32)                                                                                  \
     case G * 2 + F32: {                                                                                 \
         constexpr size_t fsm = tcore::field_smem<F32, QQ>();                                            \
         BB_TRY(b, tcore::allow_smem(k_btrace<F32, QQ>, fsm));                                           \
-        const unsigned grid = tcore::lines_grid(k_btrace<F32, QQ>, fsm, b->num_sms, total);             \
-        k_btrace<F32, QQ><<<grid, tcore::kLT, fsm, s>>>(b->d_targs, b->d_loff, n, b->d_lnext, d_seeds,  \
-                                                        d_K, d_st, d_ns);                               \
+        const unsigned grid = tcore::lines_grid(k_btrace<F32, QQ>, fsm, b->num_sms, total, ncl);        \
+        BB_TRY(b, tcore::launch_lines(k_btrace<F32, QQ>, grid, fsm, s, ncl, (const tcore::TArgs*)b->d_targs, \
+                                      (const int64_t*)b->d_loff, n, b->d_lnext, d_seeds, d_K, d_st, d_ns)); \
         break;                                                                                          \
     }
         BT(2, 4, 0) BT(2, 4, 1) BT(3, 9, 0) BT(3, 9, 1) BT(4, 16, 0) BT(4, 16, 1)

@@ -53,8 +53,10 @@ int launch(bem_ctx* c, const TArgs& A, int64_t L, const double* seeds, double* K
     case G: {                                                                                    \
         constexpr size_t fsm = field_smem<F32, QQ>();                                            \
         BEM_CUDA_TRY(c, allow_smem(k_trace<F32, QQ>, fsm));                                      \
-        const unsigned grid = lines_grid(k_trace<F32, QQ>, fsm, c->num_sms, L);                  \
-        k_trace<F32, QQ><<<grid, kLT, fsm, c->stream>>>(A, seeds, L, c->d_line_next, K, st, ns, xe); \
+        const int ncl = tracer_cluster(c->np);                                                   \
+        const unsigned grid = lines_grid(k_trace<F32, QQ>, fsm, c->num_sms, L, ncl);             \
+        BEM_CUDA_TRY(c, launch_lines(k_trace<F32, QQ>, grid, fsm, c->stream, ncl, A, seeds, L,   \
+                                     c->d_line_next, K, st, ns, xe));                            \
         break;                                                                                   \
     }
         TR_CASE(1, 1) TR_CASE(2, 4) TR_CASE(3, 9) TR_CASE(4, 16) TR_CASE(5, 25) TR_CASE(6, 36)

@@ -17,10 +17,18 @@
 // Events (branch of alpha_eff at |E| = E0, |x| = r_max, entering another electrode)
 // are located on the re-stepped RK4 step by the Illinois variant of regula falsi
 // (at most 100 iterations); a step holds at most 4 events, the whole line at most
-// max_steps steps, so every loop is bounded.  Warps synchronise only through CTA
+// max_steps steps, so every loop is bounded.  Warps synchronise through CTA
 // barriers that every warp reaches once per round (a warp without a line joins
-// the rounds until no warp has one), so nothing waits on another CTA.
+// the rounds until no warp has one).  On meshes of kSplitMin triangles or more the
+// launch is made of clusters of two CTAs: the leader runs the lines, the helper
+// sweeps the second half of the triangles in every round of its leader, and the two
+// meet at the hardware cluster barrier twice per round (the round's points pushed
+// into the helper's shared memory, the helper's partial sums pushed into the
+// leader's).  Both run the same fixed sequence of barriers, paired one to one, and
+// no CTA waits on a CTA outside its own cluster.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cmath>
@@ -29,10 +37,14 @@
 
 namespace tcore {
 
+namespace cg = cooperative_groups;
+
 constexpr int kT = 256;          // threads of the adjoint's CTA-wide passes
 constexpr int kWarps = kT / 32;
 constexpr int kLW = 8;           // lines in flight per tracer CTA, one per warp
 constexpr int kLT = 32 * kLW;    // threads per tracer CTA
+constexpr int kCl = 2;           // largest tracer cluster: the leader and its helper
+constexpr int64_t kSplitMin = 8192;  // meshes of this many triangles or more are split over a cluster
 
 struct TArgs {
     int64_t np;
@@ -84,7 +96,29 @@ struct Round {
     double N[kLW][kLW][4];  // [target][warp] closed-form pairs
     double G[kLW][kLW][4];  // [target][warp] FP64 regular pairs (times 4 pi)
     int32_t near[kLW][kLW][kNearCap];  // [warp][target slot] triangles of near pairs found
+    // cluster exchange: the leader pushes x, sr, act, args and exit into each helper's
+    // round; each helper pushes its partial sums into the leader's HF, HN, HG
+    TArgs args;
+    int exit;
+    float HF[kCl - 1][kLW][kLW][4];
+    double HN[kCl - 1][kLW][kLW][4];
+    double HG[kCl - 1][kLW][kLW][4];
 };
+
+// the triangles [j0, j1) that the cluster's CTA of this rank sweeps in every round:
+// a mesh of kSplitMin triangles or more is split into ncl parts of whole
+// 256-triangle chunks (so every copy of the staging ring stays aligned); a smaller
+// mesh is swept by the leader alone, so its sums do not depend on the cluster size
+__device__ __forceinline__ void rank_range(int64_t np, int rank, int ncl, int64_t& j0, int64_t& j1)
+{
+    const int parts = np >= kSplitMin ? ncl : 1;
+    const int64_t per = ((np + parts - 1) / parts + 255) / 256 * 256;
+    j0 = min(np, (int64_t)rank * per);
+    j1 = min(np, j0 + per);
+}
+
+// cluster size of a tracer launch over meshes of at most np triangles
+inline int tracer_cluster(int64_t np) { return np >= kSplitMin ? kCl : 1; }
 
 // The FP32 evaluation streams the triangles through shared memory in chunks of TC
 // (nodes, classification header, normal + region, density) with an NS-stage ring of
@@ -168,7 +202,7 @@ __device__ __forceinline__ void stage_chunk(const TArgs& A, Stage32<Q>& S, int b
 //  * FP64 form: one plain strided pass per slot, FP64 regular pairs, closed form in
 //    place.
 template <bool F32, int Q, int NT>
-__device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
+__device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, int64_t j0, int64_t j1)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int tk[NT];
@@ -225,13 +259,13 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
             ncnt[s] = 0;
         };
         constexpr int NS = Stage32<Q>::NS;
-        const int64_t nch = (A.np + TC - 1) / TC;
+        const int64_t nch = (j1 - j0 + TC - 1) / TC;
         const int t = threadIdx.x;
         // prologue: chunks 0 .. NS-2 in flight (one commit group per chunk, empty past the end);
         // the previous round's reads of the ring ended before the round's entry barrier
 #pragma unroll
         for (int p = 0; p < NS - 1; ++p) {
-            if (p < nch) stage_chunk<Q>(A, S, p, (int64_t)p * TC, (int)min((int64_t)TC, A.np - (int64_t)p * TC));
+            if (p < nch) stage_chunk<Q>(A, S, p, j0 + (int64_t)p * TC, (int)min((int64_t)TC, j1 - j0 - (int64_t)p * TC));
             cp_async_commit();
         }
         for (int64_t c = 0; c < nch; ++c) {
@@ -239,10 +273,10 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
             cp_async_wait<NS - 2>();  // this lane's copies of chunks 0..c have landed (NS-2 newer groups may be in flight)
             __syncwarp();             // ... for every lane of the warp; and every lane is done with chunk c-1
             const int64_t cn = c + NS - 1;  // its buffer, (c-1) % NS, takes chunk c+NS-1 now
-            if (cn < nch) stage_chunk<Q>(A, S, (int)(cn % NS), cn * TC, (int)min((int64_t)TC, A.np - cn * TC));
+            if (cn < nch) stage_chunk<Q>(A, S, (int)(cn % NS), j0 + cn * TC, (int)min((int64_t)TC, j1 - j0 - cn * TC));
             cp_async_commit();
-            const int64_t j = c * TC + t;
-            const bool valid = t < TC && j < A.np;
+            const int64_t j = j0 + c * TC + t;
+            const bool valid = t < TC && j < j1;
             bool nearf[NT];
             if (valid) {
                 const float4 nv = S.nrm[b][t];
@@ -310,7 +344,7 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
             const double* xs = R.x[k];
             const int srk = R.sr[k];
             double q[4] = {0.0, 0.0, 0.0, 0.0}, d[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int64_t j = threadIdx.x; j < A.np; j += kLT) {
+            for (int64_t j = j0 + threadIdx.x; j < j1; j += kLT) {
                 if (is_far64(xs[0], xs[1], xs[2], A.hdr64[j])) {
                     const int rj = A.region[j];
                     const double* gp = A.geo + GEO_STRIDE * j;
@@ -353,10 +387,10 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt)
     }
 }
 
-// The field at every posted point (all threads call this after the round's entry
-// barrier): the variant for the number of posting warps, rounded up to 1, 2, 4 or 8.
+// This CTA's part of the field at every posted point: the triangles [j0, j1), the
+// variant for the number of posting warps, rounded up to 1, 2, 4 or 8.
 template <bool F32, int Q>
-__device__ __noinline__ void eval_round(const TArgs& A, Round& R)
+__device__ __noinline__ void sweep(const TArgs& A, Round& R, int64_t j0, int64_t j1)
 {
     unsigned amask = 0u;
 #pragma unroll
@@ -365,15 +399,82 @@ __device__ __noinline__ void eval_round(const TArgs& A, Round& R)
     const int nt = __popc(amask);
     if (nt == 0) return;
     if constexpr (!F32) {
-        eval_targets<F32, Q, 1>(A, R, amask, nt);  // the FP64 form loops over the slots
+        eval_targets<F32, Q, 1>(A, R, amask, nt, j0, j1);  // the FP64 form loops over the slots
     } else if (nt == 1) {
-        eval_targets<F32, Q, 1>(A, R, amask, nt);
+        eval_targets<F32, Q, 1>(A, R, amask, nt, j0, j1);
     } else if (nt == 2) {
-        eval_targets<F32, Q, 2>(A, R, amask, nt);
+        eval_targets<F32, Q, 2>(A, R, amask, nt, j0, j1);
     } else if (nt <= 4) {
-        eval_targets<F32, Q, 4>(A, R, amask, nt);
+        eval_targets<F32, Q, 4>(A, R, amask, nt, j0, j1);
     } else {
-        eval_targets<F32, Q, 8>(A, R, amask, nt);
+        eval_targets<F32, Q, 8>(A, R, amask, nt, j0, j1);
+    }
+}
+
+// A round of the cluster, on the leader (all its threads call this after the round's
+// entry barrier, with at least one point posted): push the posted points and the
+// arguments into every helper's round, meet the helpers at the cluster barrier,
+// sweep the leader's part of the triangles, and meet them again -- by then every
+// helper has pushed its partial sums into R.HF, R.HN, R.HG.
+template <bool F32, int Q>
+__device__ void eval_round(const TArgs& A, Round& R)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncl = (int)cl.num_blocks();
+    for (int h = 1; h < ncl; ++h) {
+        Round* Rh = cl.map_shared_rank(&R, h);
+        for (int i = threadIdx.x; i < kLW * 3; i += kLT) Rh->x[i / 3][i % 3] = R.x[i / 3][i % 3];
+        if (threadIdx.x < kLW) {
+            Rh->sr[threadIdx.x] = R.sr[threadIdx.x];
+            Rh->act[threadIdx.x] = R.act[threadIdx.x];
+        }
+        if (threadIdx.x == 0) {
+            Rh->args = A;
+            Rh->exit = 0;
+        }
+    }
+    cl.sync();
+    int64_t j0, j1;
+    rank_range(A.np, 0, ncl, j0, j1);
+    sweep<F32, Q>(A, R, j0, j1);
+    cl.sync();
+}
+
+// The leader's last act: the helpers leave their loop.
+__device__ __forceinline__ void release_helpers(Round& R)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x == 0)
+        for (int h = 1; h < (int)cl.num_blocks(); ++h) cl.map_shared_rank(&R, h)->exit = 1;
+    cl.sync();
+}
+
+// A helper CTA (cluster rank >= 1): one iteration per round of its leader -- wait for
+// the pushed round, sweep this rank's part of the triangles for the posted points,
+// push the partial sums into the leader's round, meet the leader again.  Its barriers
+// pair one to one with the leader's (two per round, one at the release), so the two
+// CTAs go through the same sequence of cluster barriers.  A CTA only writes the
+// other's shared memory and reads its own.
+template <bool F32, int Q>
+__device__ void helper_rounds(Round& R, int rank)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    Round* R0 = cl.map_shared_rank(&R, 0);
+    for (;;) {
+        cl.sync();                    // the leader has pushed a round, or the release
+        if (R.exit) break;
+        int64_t j0, j1;
+        rank_range(R.args.np, rank, (int)cl.num_blocks(), j0, j1);
+        sweep<F32, Q>(R.args, R, j0, j1);
+        cta_bar();                    // every warp's partial sums are in R
+        for (int i = threadIdx.x; i < kLW * kLW * 4; i += kLT) {
+            const int k = i / (kLW * 4), w = (i / 4) % kLW, c = i % 4;
+            if (!R.act[k]) continue;
+            R0->HF[rank - 1][k][w][c] = R.F[k][w][c];
+            R0->HN[rank - 1][k][w][c] = R.N[k][w][c];
+            R0->HG[rank - 1][k][w][c] = R.G[k][w][c];
+        }
+        cl.sync();                    // the leader may read them
     }
 }
 
@@ -389,6 +490,11 @@ __device__ __forceinline__ V4 round_result(const Round& R, int w)
 #pragma unroll
     for (int u = 0; u < kLW; ++u)
         v += a == 0 ? (double)R.F[w][u][c] : (a == 1 ? R.N[w][u][c] : R.G[w][u][c]);
+    // the helper's part (a cluster of two)
+    if (cg::this_cluster().num_blocks() > 1)
+#pragma unroll
+        for (int u = 0; u < kLW; ++u)
+            v += a == 0 ? (double)R.HF[0][w][u][c] : (a == 1 ? R.HN[0][w][u][c] : R.HG[0][w][u][c]);
     double f[4], n[4], g[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -646,13 +752,23 @@ __device__ void trace_line(const TArgs& A, Round& R, const double* xs, Rec& rec,
 // in the first round in which no warp posts a point (all warps together), and moves
 // to another mesh with lines left.  The counters only grow, so the loops end.
 // s_int: three shared ints (current mesh, lines held, no-lines-left flag).
+// The CTAs of a launch form clusters of 1 or kCl: the leader (rank 0) runs this loop, and
+// every round it evaluates is shared with the helpers (eval_round); a helper runs
+// helper_rounds until the leader releases it.
 template <bool F32, int Q, class ArgsFn, class CountFn, class LineFn>
 __device__ void run_lines(ArgsFn args, CountFn L, int ninst, int64_t total, unsigned long long* next,
                           TArgs& sA, Round& R, int* s_int, LineFn line_fn)
 {
+    const int rank = (int)cg::this_cluster().block_rank();
+    if (rank != 0) {
+        helper_rounds<F32, Q>(R, rank);
+        return;
+    }
     const int lane = threadIdx.x & 31;
-    const int cap = (int)min((int64_t)kLW, max((int64_t)1, (total + gridDim.x - 1) / (int64_t)gridDim.x));
-    int start = (int)(blockIdx.x % (unsigned)ninst);
+    const int ncl = (int)cg::this_cluster().num_blocks();
+    const int64_t nlead = gridDim.x / ncl;  // clusters of the launch
+    const int cap = (int)min((int64_t)kLW, max((int64_t)1, (total + nlead - 1) / nlead));
+    int start = (int)((blockIdx.x / ncl) % (unsigned)ninst);
     for (;;) {
         if (threadIdx.x == 0) {
             int pick = -1;
@@ -701,21 +817,42 @@ __device__ void run_lines(ArgsFn args, CountFn L, int ninst, int64_t total, unsi
         start = ci;
         cta_bar();  // sA and s_int are rewritten next
     }
+    release_helpers(R);
 }
 
-// persistent grid of a tracer kernel: every resident CTA slot of the GPU, but never
-// more CTAs than lines (with the per-CTA cap of run_lines, few lines spread one per
-// CTA, many lines fill every warp)
+// persistent grid of a tracer kernel, in whole clusters: every resident CTA slot of
+// the GPU, but never more clusters than lines (with the per-cluster cap of run_lines,
+// few lines spread one per cluster, many lines fill every warp)
 template <class Kernel>
-inline unsigned lines_grid(Kernel k, size_t smem, int num_sms, int64_t lines)
+inline unsigned lines_grid(Kernel k, size_t smem, int num_sms, int64_t lines, int ncl)
 {
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kLT, smem) != cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;
     }
-    const int64_t slots = (int64_t)num_sms * std::max(per_sm, 1);
-    return (unsigned)std::max<int64_t>(1, std::min(slots, lines));
+    const int64_t clusters = (int64_t)num_sms * std::max(per_sm, 1) / ncl;
+    return (unsigned)(ncl * std::max<int64_t>(1, std::min(clusters, lines)));
+}
+
+// launch a tracer kernel as clusters of ncl CTAs (1: plain CTAs)
+template <class... KArgs, class... Args>
+inline cudaError_t launch_lines(void (*kernel)(KArgs...), unsigned grid, size_t smem, cudaStream_t s, int ncl,
+                                Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kLT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ncl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 }  // namespace tcore
