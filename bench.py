@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--batch-points", type=int, default=10000,
                     help="batch mode: field points per mesh for bem_batch_eval_field")
     ap.add_argument("--max-steps", type=int, default=200000, help="trace mode: RK4 step limit per line")
+    ap.add_argument("--no-trace", action="store_true", help="skip the field-line block of the step's line")
+    ap.add_argument("--trace-cluster", default="0",
+                    help="trace mode: CTAs per tracer cluster (0 automatic); a comma list runs each")
     ap.add_argument("--instances", type=int, default=64, help="batch mode: meshes in the family")
     ap.add_argument("--nrhs", type=int, default=4, help="batch mode: right-hand sides per mesh")
     ap.add_argument("--seeds", type=int, default=8, help="batch mode: field lines traced per mesh")
@@ -414,6 +417,9 @@ def run_ours(args):
     roofline["tuning"] = ctx.tuning()   # the kernel shape bem_create's tuner chose, and the candidates' times
 
     rel = out["rel"][0]
+    # the true residual of the step's result, with the double-FP32 product (untimed)
+    b0 = ctx.rhs()[0]
+    true_rel = ((b0 - ctx.matvec(out["u"][0], precision=bem.DF)).norm() / b0.norm()).item()
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "f32 regular pairs + f64",
@@ -422,7 +428,8 @@ def run_ours(args):
                                   {"gmres_iters_per_step": cnt["gmres_iters"] / args.steps,
                                    "products_per_step": {"mixed": cnt["matvecs"][1] / args.steps,
                                                          "double_fp32_residual": cnt["matvecs"][2] / args.steps},
-                                   "fp64_relres": rel, "pairs_per_step": pairs_step}),
+                                   "relres": rel, "relres_recomputed_double_fp32": true_rel,
+                                   "pairs_per_step": pairs_step}),
               "roofline": roofline, "gpu_launches": launches}
     if clk:
         result["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
@@ -431,6 +438,9 @@ def run_ours(args):
         result["fp64_form"] = fp64_form(args, bem, ctx, mesh, pts_d, out, cnt, ms, stream, flush)
     if not args.no_c2 and rank == 0 and mesh.np_ > 100000:
         result["c2"] = c2_block(args, bem, stream, flush)
+
+    if not args.no_trace and rank == 0:
+        result["trace"] = trace_block(args, bem)
 
     if not args.no_e2e:
         result["e2e"] = e2e_block(args, bem, mesh, pts, dev, flush, dist, world, pairs_step)
@@ -495,6 +505,40 @@ def fp64_form(args, bem, ctx, mesh, pts_d, out, cnt, ms_mixed, stream, flush):
             "E_rel_mixed_vs_fp64_on_sample": dE}
 
 
+def trace_block(args, bem):
+    """Field lines beside the step (untimed by the step's clock, CUDA events of their own):
+    c3's 256 Fibonacci lines on the 1,280-triangle sphere (h = 1e-3, r_max = 10), and
+    1,024 lines seeded on |x| = 1.05 around the conductor sphere of the 20k device; both
+    mixed, each after a warm-up call on 8 lines."""
+    import torch
+    from paper_2003_12663_gb300 import meshgen as mg
+    out = {}
+    for key, mesh, seeds in (("c3_sphere_256_lines", mg.sphere_mesh(3), mg.fibonacci_seeds(256)),
+                             ("device20k_1024_lines", mg.device_mesh(1.0, seed=2),
+                              mg.fibonacci_seeds(1024, radius=1.05))):
+        ctx = bem.Context(mesh)
+        u, _, _ = ctx.solve(bem.MIXED, tol=1e-10)
+        sd = torch.tensor(seeds)
+        ctx.trace_lines(u[0], sd[:8], bem.MIXED)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        K, st, ns, _ = ctx.trace_lines(u[0], sd, bem.MIXED)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        steps = int(ns.sum().item())
+        Q = ctx.params.far_order ** 2
+        out[key] = {"triangles": int(mesh.np_), "lines": len(seeds), "ms": ms, "rk4_steps": steps,
+                    "field_pair_ops_per_s": steps * 4 * mesh.np_ * Q / (ms * 1e-3),
+                    "max_steps_of_a_line": int(ns.max().item()),
+                    "lines_reaching_r_max": int((st == 1).sum().item())}
+        ctx.close()
+    out["note"] = ("field pair-ops: RK4 steps x 4 field evaluations x triangles x nodes "
+                   "(event re-steps not counted)")
+    return out
+
+
 def c2_block(args, bem, stream, flush):
     """The same step on the 20k device, both GPU forms, each the median of 5 runs."""
     import torch
@@ -523,37 +567,43 @@ def c2_block(args, bem, stream, flush):
     u32, it32, rel32, E32 = res["mixed"]
     u64, it64, rel64, E64 = res["fp64"]
     c.close()
-    # the mixed form with the refinement residual in FP64 instead of double-FP32
-    cf = bem.Context(mesh, residual=bem.RESIDUAL_FP64)
-    resf = {}
+    # the mixed form with every refinement residual in FP64, or in double-FP32, instead
+    # of the default (the first in double-FP32, the later ones updated)
+    alt = {}
+    for key, mode in (("mixed_with_fp64_residual", bem.RESIDUAL_FP64),
+                      ("mixed_with_double_fp32_residual_every_step", bem.RESIDUAL_DF)):
+        cf = bem.Context(mesh, residual=mode)
+        resf = {}
 
-    def stepf():
-        u, it, rel = cf.solve(bem.MIXED, tol=TOL)
-        cf.surface_field(u[0], bem.MIXED)
-        phi, E = cf.eval_field(u[0], pts_d, bem.MIXED)
-        resf.update(u=u, it=it, rel=rel, E=E)
+        def stepf():
+            u, it, rel = cf.solve(bem.MIXED, tol=TOL)
+            cf.surface_field(u[0], bem.MIXED)
+            phi, E = cf.eval_field(u[0], pts_d, bem.MIXED)
+            resf.update(u=u, it=it, rel=rel, E=E)
 
-    stepf()
-    tf = events_ms(stepf, stream, 3, flush)
-    cf.close()
-    mf = float(np.median(tf))
+        stepf()
+        tf = events_ms(stepf, stream, 3, flush)
+        cf.close()
+        alt[key] = {
+            "ms_per_step": float(np.median(tf)), "runs_ms": tf, "statistic": "median of 3",
+            "gmres_iters": resf["it"], "relres": resf["rel"][0],
+            "sigma_rel_l2_vs_fp64": (torch.linalg.norm(resf["u"][0] - u64[0]) / torch.linalg.norm(u64[0])).item(),
+            "E_rel_vs_fp64": ((resf["E"] - E64).abs().max() / E64.abs().max()).item(),
+            "sigma_rel_l2_vs_default_residual":
+                (torch.linalg.norm(resf["u"][0] - u32[0]) / torch.linalg.norm(u32[0])).item()}
     m32, m64 = float(np.median(t32)), float(np.median(t64))
-    return {"workload": workload_name(mesh), "triangles": int(mesh.np_), "eval_points": len(pts),
-            "statistic": "median of 5 runs (CUDA events), L2 flushed before each",
-            "mixed": {"ms_per_step": m32, "runs_ms": t32, "gmres_iters": it32, "relres": rel32[0],
-                      "value": pairs_step / (m32 * 1e-3) / 1e9, "unit": UNIT},
-            "fp64": {"ms_per_step": m64, "runs_ms": t64, "gmres_iters": it64, "relres": rel64[0],
-                     "value": pairs64 / (m64 * 1e-3) / 1e9, "unit": UNIT},
-            "mixed_speedup": m64 / m32,
-            "sigma_rel_l2_mixed_vs_fp64": (torch.linalg.norm(u32[0] - u64[0]) / torch.linalg.norm(u64[0])).item(),
-            "E_rel_mixed_vs_fp64": ((E32 - E64).abs().max() / E64.abs().max()).item(),
-            "mixed_with_fp64_residual": {
-                "ms_per_step": mf, "runs_ms": tf, "statistic": "median of 3", "gmres_iters": resf["it"],
-                "relres": resf["rel"][0],
-                "sigma_rel_l2_vs_fp64": (torch.linalg.norm(resf["u"][0] - u64[0]) / torch.linalg.norm(u64[0])).item(),
-                "E_rel_vs_fp64": ((resf["E"] - E64).abs().max() / E64.abs().max()).item(),
-                "sigma_rel_l2_vs_double_fp32_residual":
-                    (torch.linalg.norm(resf["u"][0] - u32[0]) / torch.linalg.norm(u32[0])).item()}}
+    out = {"workload": workload_name(mesh), "triangles": int(mesh.np_), "eval_points": len(pts),
+           "statistic": "median of 5 runs (CUDA events), L2 flushed before each",
+           "mixed": {"ms_per_step": m32, "runs_ms": t32, "gmres_iters": it32, "relres": rel32[0],
+                     "residual": "first in double-FP32, later ones updated with the correction's mixed product",
+                     "value": pairs_step / (m32 * 1e-3) / 1e9, "unit": UNIT},
+           "fp64": {"ms_per_step": m64, "runs_ms": t64, "gmres_iters": it64, "relres": rel64[0],
+                    "value": pairs64 / (m64 * 1e-3) / 1e9, "unit": UNIT},
+           "mixed_speedup": m64 / m32,
+           "sigma_rel_l2_mixed_vs_fp64": (torch.linalg.norm(u32[0] - u64[0]) / torch.linalg.norm(u64[0])).item(),
+           "E_rel_mixed_vs_fp64": ((E32 - E64).abs().max() / E64.abs().max()).item()}
+    out.update(alt)
+    return out
 
 
 def e2e_block(args, bem, mesh, pts, dev, flush, dist, world, pairs_step):
@@ -745,26 +795,28 @@ def run_trace(args):
     from paper_2003_12663_gb300 import bem
     from paper_2003_12663_gb300 import meshgen as mg
     mesh = mg.device_mesh(args.scale if args.scale is not None else 1.0, seed=2)
-    ctx = bem.Context(mesh)
-    u, _, _ = ctx.solve(bem.MIXED, tol=TOL)
     seeds = torch.tensor(mg.fibonacci_seeds(args.lines, radius=args.seed_radius))
-    ctx.trace_lines(u[0], seeds[:8], bem.MIXED, max_steps=args.max_steps)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    K, st, ns, xe = ctx.trace_lines(u[0], seeds, bem.MIXED, max_steps=args.max_steps)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    steps = int(ns.sum().item())
-    Q = ctx.params.far_order ** 2
-    print(json.dumps({"mode": "trace", "triangles": ctx.np, "lines": args.lines, "seed_radius": args.seed_radius,
-                      "ms": ms,
-                      "lines_per_s": args.lines / (ms * 1e-3), "rk4_steps": steps,
-                      "field_pair_ops_per_s": steps * 4 * ctx.np * Q / (ms * 1e-3),
-                      "status_counts": {int(k): int(v) for k, v in
-                                        zip(*np.unique(st.cpu().numpy(), return_counts=True))}}), flush=True)
-    ctx.close()
+    for ncl in [int(v) for v in str(args.trace_cluster).split(",")]:
+        ctx = bem.Context(mesh, trace_cluster=ncl)
+        u, _, _ = ctx.solve(bem.MIXED, tol=TOL)
+        ctx.trace_lines(u[0], seeds[:8], bem.MIXED, max_steps=args.max_steps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        K, st, ns, xe = ctx.trace_lines(u[0], seeds, bem.MIXED, max_steps=args.max_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        steps = int(ns.sum().item())
+        Q = ctx.params.far_order ** 2
+        print(json.dumps({"mode": "trace", "triangles": ctx.np, "lines": args.lines,
+                          "seed_radius": args.seed_radius, "trace_cluster": ncl, "ms": ms,
+                          "lines_per_s": args.lines / (ms * 1e-3), "rk4_steps": steps,
+                          "field_pair_ops_per_s": steps * 4 * ctx.np * Q / (ms * 1e-3),
+                          "K_sum": float(K.sum().item()), "max_steps_of_a_line": int(ns.max().item()),
+                          "status_counts": {int(k): int(v) for k, v in
+                                            zip(*np.unique(st.cpu().numpy(), return_counts=True))}}), flush=True)
+        ctx.close()
 
 
 # ------------------------------------------------------------------ per-configuration report

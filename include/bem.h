@@ -96,8 +96,8 @@ typedef struct {
     int32_t max_refine;      /* BEM_MIXED: iterative-refinement steps; default 6 */
     int64_t max_points;      /* largest M of one bem_eval_field chunk; default 131072 */
     int32_t timing;          /* != 0: time every regular-pair kernel with CUDA events (bem_counters) */
-    int32_t residual;        /* BEM_MIXED refinement residual b - A u: BEM_RESIDUAL_DF (default)
-                                or BEM_RESIDUAL_FP64 */
+    int32_t residual;        /* BEM_MIXED refinement residual b - A u: BEM_RESIDUAL_DF_UPDATE
+                                (default), BEM_RESIDUAL_DF or BEM_RESIDUAL_FP64 */
     int32_t far32_variant;   /* FP32 regular-pair kernel: 1 scalar, 2 or 4 packed target pairs
                                 per thread; 0 (default): bem_create times the candidates on the
                                 mesh's own matvec and keeps the fastest (N >= 4096; else 2) */
@@ -109,14 +109,24 @@ typedef struct {
                                 buffers of at most 64 MiB, the transposed operator's near pairs
                                 by column) is allocated by bem_create; 0: none (bem_adjoint and
                                 bem_matvec_transpose then return BEM_ERR_CAPACITY); default 256 */
+    int32_t trace_cluster;   /* CTAs per tracer cluster, 1..8: on meshes of 8192 triangles or
+                                more every round's triangles are split over them; 0 (default):
+                                chosen per launch from the mesh size and the number of lines
+                                (wide clusters for few lines, plain CTAs for many) */
 } bem_params;
 
 /* How the iterative refinement of BEM_MIXED forms its residual b - A u.
  * BEM_RESIDUAL_FP64: the FP64 regular-pair kernel.  BEM_RESIDUAL_DF: the same pairs
  * in double-FP32 arithmetic (an unevaluated sum of two floats, error-free
  * transformations of Dekker and Knuth) on the FP32 units, about 1e-13 relative per
- * pair, with the pair classification of the FP64 form reproduced exactly. */
-enum { BEM_RESIDUAL_DF = 0, BEM_RESIDUAL_FP64 = 1 };
+ * pair, with the pair classification of the FP64 form reproduced exactly.
+ * BEM_RESIDUAL_DF_UPDATE (default): the first residual of a solve in double-FP32; each
+ * later one as r - A d, the previous residual less the mixed product of the step's
+ * correction d, while |d| <= 1e-3 |u| (else in double-FP32 again).  The product's FP32
+ * rounding, about 1e-7 |A| |d|, is then below 1e-10 |A| |u|: the true residual of the
+ * result differs from the one the refinement stops on by that much, and the solve
+ * needs one double-FP32 pass instead of one per refinement step. */
+enum { BEM_RESIDUAL_DF = 0, BEM_RESIDUAL_FP64 = 1, BEM_RESIDUAL_DF_UPDATE = 2 };
 
 /* Work done by a context since creation or the last bem_reset_counters.
  * Index [BEM_FP64] / [BEM_MIXED] / [2] = double-FP32 residual pass. */

@@ -49,10 +49,10 @@ class bem_params(ctypes.Structure):
                 ("max_refine", ctypes.c_int32), ("max_points", ctypes.c_int64),
                 ("timing", ctypes.c_int32), ("residual", ctypes.c_int32),
                 ("far32_variant", ctypes.c_int32), ("adjoint_checkpoint", ctypes.c_int32),
-                ("adjoint_lines", ctypes.c_int64)]
+                ("adjoint_lines", ctypes.c_int64), ("trace_cluster", ctypes.c_int32)]
 
 
-RESIDUAL_DF, RESIDUAL_FP64 = 0, 1
+RESIDUAL_DF, RESIDUAL_FP64, RESIDUAL_DF_UPDATE = 0, 1, 2
 
 
 class bem_trace_params(ctypes.Structure):

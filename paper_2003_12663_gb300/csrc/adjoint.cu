@@ -1144,7 +1144,9 @@ static int adjoint_run(bem_ctx* c, const TArgs& A, int64_t L, const double* seed
     constexpr size_t fsm = field_smem<F32, Q>();
     BEM_CUDA_TRY(c, allow_smem(k_adj_forward<F32, Q>, fsm));
     BEM_CUDA_TRY(c, allow_smem(k_adj_resume<F32, Q>, fsm));
-    const int ncl = tracer_cluster(np);  // the cluster size of bem_trace_lines on this mesh
+    // one cluster size for the forward pass and every recomputed segment, so the
+    // segments retrace the forward trajectories bit for bit
+    const int ncl = tracer_cluster(np, chunk, c->num_sms, c->prm.trace_cluster);
     BEM_CUDA_TRY(c, cudaMemsetAsync(W.gu, 0, c->nunk * sizeof(double), s));
     BEM_CUDA_TRY(c, cudaMemsetAsync(W.gPt, 0, 9 * np * sizeof(double), s));
     std::vector<int64_t> h_n(chunk);

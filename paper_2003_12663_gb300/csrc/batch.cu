@@ -789,7 +789,7 @@ extern "C" int bem_batch_create(bem_batch** out, bem_ctx* const* ctxs, int32_t n
     b->m = ctxs[0]->m;
     b->max_it = ctxs[0]->prm.max_iters;
     b->max_refine = ctxs[0]->prm.max_refine;
-    b->rprec = ctxs[0]->prm.residual == BEM_RESIDUAL_DF ? kPrecDF : BEM_FP64;
+    b->rprec = ctxs[0]->prm.residual == BEM_RESIDUAL_FP64 ? BEM_FP64 : kPrecDF;
     b->num_sms = std::max(ctxs[0]->num_sms, 1);
     b->timing = flags & 1;
     b->far_per_sm = far_blocks_per_sm(b->g, b->nr);
@@ -1270,11 +1270,12 @@ extern "C" int bem_batch_trace(bem_batch* b, int32_t precision, const double* co
     int32_t* const* d_st = (int32_t* const*)(b->d_tptr + 2 * n);
     int32_t* const* d_ns = (int32_t* const*)(b->d_tptr + 3 * n);
     int rc = BEM_OK;
-    // clusters of two CTAs when any mesh is large enough to be split (a smaller mesh is
-    // still swept by the leader alone, exactly as in its own bem_trace_lines)
+    // the cluster size for the largest mesh and all lines (the first instance's
+    // trace_cluster, if set); a mesh too small to be split is swept by the leader alone,
+    // exactly as in its own bem_trace_lines
     int64_t npmax = 0;
     for (int i = 0; i < n; ++i) npmax = std::max(npmax, b->ctx[i]->np);
-    const int ncl = tcore::tracer_cluster(npmax);
+    const int ncl = tcore::tracer_cluster(npmax, total, b->num_sms, b->ctx[0]->prm.trace_cluster);
     switch (b->g * 2 + (precision == BEM_MIXED ? 1 : 0)) {
 #define BT(G, QQ, F32)                                                                                  \
     case G * 2 + F32: {                                                                                 \

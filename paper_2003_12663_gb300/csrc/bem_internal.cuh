@@ -97,6 +97,12 @@ struct bem_ctx {
     double* field = nullptr;       // [kMaxRhs][np][4] reduced phi, E at the centroids
     double* neut = nullptr;        // [kMaxRhs][np] neutrality contributions
     double* pts_stage = nullptr;   // staging for host points (unused by device-pointer calls)
+    // spatial order of one chunk of evaluation points (order.cu)
+    double* ord_pts = nullptr;     // [max_points][3] the points in cell order
+    int32_t* ord_perm = nullptr;   // [max_points] input index of each ordered point
+    int32_t* ord_cell = nullptr;   // [max_points] cell of each input point
+    int32_t* ord_hist = nullptr;   // [order_hist_len] per-block cell counts, then offsets
+    float* ord_box = nullptr;      // [order_box_len] partial bounding boxes
 
     // solver workspace
     int m = 100;
@@ -268,6 +274,10 @@ int launch_far(bem_ctx* ctx, int precision, const FarTargets& T, const double* u
                int64_t ustride, int splits, double* part);
 
 // field.cu
+constexpr int64_t kOrderMin = 4096;  // bem_eval_field orders chunks of at least this many points
+int64_t order_hist_len(int64_t max_points);
+int64_t order_box_len();
+int order_points(bem_ctx* c, int64_t M, const double* pts, double* spts, int32_t* perm);
 int launch_points_near(bem_ctx* ctx, int precision, int64_t M, const double* pts, const double* u,
                        const double* part, int splits, double* phi, double* E);
 // need_E: also fill ctx->field with E at the conductor rows (otherwise their regular

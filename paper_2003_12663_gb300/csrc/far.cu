@@ -285,7 +285,7 @@ k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_
                                      dz = __fadd2_rn(tz[q], mz);
                         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
                         const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-                        cp[q][0] = __fadd2_rn(cp[q][0], __fmul2_rn(w2, ri));
+                        cp[q][0] = __ffma2_rn(w2, ri, cp[q][0]);
                     }
                 }
             }
@@ -325,8 +325,7 @@ k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_
                                      dz = __fadd2_rn(tz[q], mz);
                         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
                         const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-                        const float2 t = __fmul2_rn(w2, ri);
-                        ps[q] = k == 0 ? t : __fadd2_rn(ps[q], t);
+                        ps[q] = k == 0 ? __fmul2_rn(w2, ri) : __ffma2_rn(w2, ri, ps[q]);
                     }
                 }
                 const float4 h = s_hdr[p];

@@ -111,12 +111,14 @@ __global__ void k_rhs(int64_t np, int64_t nunk, int nregions, const int32_t* __r
 // with the classification of the regular pass (so that every pair is taken
 // exactly once), gathers the near ones in shared memory and evaluates them 32 at
 // a time with the FP64 closed form; then adds the far partials of all splits.
+// perm (or NULL): point t's results go to slot perm[t] of phi and E.
 template <bool F32>
 __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* __restrict__ pts,
                               const float4* __restrict__ hdr32, const double4* __restrict__ hdr64,
                               const double* __restrict__ geo, const double* __restrict__ u,
                               const double* __restrict__ part, double* __restrict__ phi,
-                              double* __restrict__ E, unsigned long long* __restrict__ near_count)
+                              double* __restrict__ E, unsigned long long* __restrict__ near_count,
+                              const int32_t* __restrict__ perm)
 {
     constexpr int WARPS = 4;
     __shared__ int32_t s_list[WARPS][64];
@@ -169,8 +171,9 @@ __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* _
     ez = warp_sum(ez) + kInv4Pi * warp_sum(fz);
     if (lane == 0) {
         atomicAdd(near_count, (unsigned long long)total);
-        if (phi) phi[t] = p;
-        if (E) { E[3 * t] = ex; E[3 * t + 1] = ey; E[3 * t + 2] = ez; }
+        const int64_t o = perm ? (int64_t)perm[t] : t;
+        if (phi) phi[o] = p;
+        if (E) { E[3 * o] = ex; E[3 * o + 1] = ey; E[3 * o + 2] = ez; }
     }
 }
 
@@ -479,11 +482,11 @@ int launch_points_near(bem_ctx* c, int precision, int64_t M, const double* pts, 
     if (precision == BEM_MIXED)
         k_points_near<true><<<blocks, 128, 0, c->stream>>>(M, c->np, splits, pts, c->hdr32,
                                                              c->hdr64, c->geo, u, part, phi, E,
-                                                             c->d_near_count + BEM_MIXED);
+                                                             c->d_near_count + BEM_MIXED, nullptr);
     else
         k_points_near<false><<<blocks, 128, 0, c->stream>>>(M, c->np, splits, pts, c->hdr32,
                                                               c->hdr64, c->geo, u, part, phi, E,
-                                                              c->d_near_count + BEM_FP64);
+                                                              c->d_near_count + BEM_FP64, nullptr);
     BEM_LAUNCH_CHECK(c);
     return BEM_OK;
 }
@@ -501,18 +504,28 @@ extern "C" int bem_eval_field(bem_ctx* c, int32_t precision, const double* u, in
         const int splits = far_splits(c, precision, mc);
         if ((size_t)splits * mc * 4 > c->part_cap)
             return set_err(c, BEM_ERR_CAPACITY, "far workspace too small");
-        FarTargets T{nullptr, nullptr, nullptr, pts + 3 * m0, mc};
+        // the packed FP32 kernel takes the chunk's points in spatial order (order.cu):
+        // its tiles of consecutive points are then compact, so most triangle chunks
+        // are summed without per-pair classification
+        const double* cp = pts + 3 * m0;
+        const int32_t* perm = nullptr;
+        if (precision == BEM_MIXED && c->far32_tp >= 2 && mc >= kOrderMin) {
+            if (int rc = order_points(c, mc, cp, c->ord_pts, c->ord_perm)) return rc;
+            cp = c->ord_pts;
+            perm = c->ord_perm;
+        }
+        FarTargets T{nullptr, nullptr, nullptr, cp, mc};
         int rc = launch_far(c, precision, T, u, 1, 0, splits, c->part);
         if (rc) return rc;
         const unsigned blocks = (unsigned)((mc + 3) / 4);
         if (precision == BEM_MIXED)
             k_points_near<true><<<blocks, 128, 0, c->stream>>>(
-                mc, c->np, splits, pts + 3 * m0, c->hdr32, c->hdr64, c->geo, u, c->part,
-                phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr, c->d_near_count + BEM_MIXED);
+                mc, c->np, splits, cp, c->hdr32, c->hdr64, c->geo, u, c->part,
+                phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr, c->d_near_count + BEM_MIXED, perm);
         else
             k_points_near<false><<<blocks, 128, 0, c->stream>>>(
-                mc, c->np, splits, pts + 3 * m0, c->hdr32, c->hdr64, c->geo, u, c->part,
-                phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr, c->d_near_count + BEM_FP64);
+                mc, c->np, splits, cp, c->hdr32, c->hdr64, c->geo, u, c->part,
+                phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr, c->d_near_count + BEM_FP64, perm);
         BEM_LAUNCH_CHECK(c);
     }
     return BEM_OK;

@@ -394,7 +394,8 @@ static void free_ctx(bem_ctx* c)
                     c->zvec, c->rvec, c->bvec, c->dvec, c->ivec, c->hcol, c->d_status,
                     c->d_near_count, c->node_lo32, c->tgt_lo32, c->near_val_df, c->d_region,
                     c->d_electrode, c->qnode, c->chunk_sph, c->csc_ptr, c->csc_row, c->csc_ent,
-                    c->tsrc64, c->tsrc32, c->nrm32, c->d_line_next, c->u32};
+                    c->tsrc64, c->tsrc32, c->nrm32, c->d_line_next, c->u32, c->ord_pts,
+                    c->ord_perm, c->ord_cell, c->ord_hist, c->ord_box};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hcol_host) cudaFreeHost(c->hcol_host);
@@ -474,9 +475,10 @@ extern "C" void bem_default_params(bem_params* p)
     p->max_refine = 6;
     p->max_points = 131072;
     p->timing = 0;
-    p->residual = BEM_RESIDUAL_DF;
+    p->residual = BEM_RESIDUAL_DF_UPDATE;
     p->adjoint_checkpoint = 128;
     p->adjoint_lines = 256;
+    p->trace_cluster = 0;
 }
 
 extern "C" const char* bem_last_error(const bem_ctx* ctx)
@@ -838,7 +840,12 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
         (rc = dalloc(c, &c->zvec, n)) || (rc = dalloc(c, &c->rvec, n)) ||
         (rc = dalloc(c, &c->bvec, n)) || (rc = dalloc(c, &c->dvec, n)) ||
         (rc = dalloc(c, &c->ivec, n)) ||
-        (rc = dalloc(c, &c->hcol, 2 * (c->m + 2))))
+        (rc = dalloc(c, &c->hcol, 2 * (c->m + 2))) ||
+        (rc = dalloc(c, &c->ord_pts, 3 * (size_t)c->prm.max_points)) ||
+        (rc = dalloc(c, &c->ord_perm, (size_t)c->prm.max_points)) ||
+        (rc = dalloc(c, &c->ord_cell, (size_t)c->prm.max_points)) ||
+        (rc = dalloc(c, &c->ord_hist, (size_t)order_hist_len(c->prm.max_points))) ||
+        (rc = dalloc(c, &c->ord_box, (size_t)order_box_len())))
         return rc;
     if (cudaMallocHost((void**)&c->hcol_host, 2 * (c->m + 2) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -867,9 +874,10 @@ extern "C" int bem_create(bem_ctx** out, const bem_mesh* mesh, const bem_params*
         bem_default_params(&prm);
     if (!(prm.eta >= 1.0) || prm.far_order < 1 || prm.far_order > kMaxOrder ||
         prm.gmres_restart < 1 || prm.gmres_restart > 1000 || prm.max_iters < 1 ||
-        prm.adjoint_lines < 0 || prm.adjoint_checkpoint < 1 ||
-        prm.max_refine < 1 || prm.max_points < 1 ||
-        (prm.residual != BEM_RESIDUAL_DF && prm.residual != BEM_RESIDUAL_FP64) ||
+        prm.adjoint_lines < 0 || prm.adjoint_checkpoint < 1 || prm.trace_cluster < 0 || prm.trace_cluster > 8 ||
+        prm.max_refine < 1 || prm.max_points < 1 || prm.max_points > INT32_MAX ||
+        (prm.residual != BEM_RESIDUAL_DF && prm.residual != BEM_RESIDUAL_FP64 &&
+         prm.residual != BEM_RESIDUAL_DF_UPDATE) ||
         (prm.far32_variant != 0 && prm.far32_variant != 1 && prm.far32_variant != 2 &&
          prm.far32_variant != 4))
         return set_err(nullptr, BEM_ERR_ARG, "bad parameters (need eta >= 1, 1 <= far_order <= %d)",

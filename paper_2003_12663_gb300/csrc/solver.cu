@@ -2,7 +2,9 @@
 // need only matrix-vector products; Sec. 5: GMRES with a diagonal
 // preconditioner) on the matrix-free matvec, and, for BEM_MIXED, an iterative
 // refinement whose residual b - A u is formed with the FP64 form's operator (in
-// double-FP32 arithmetic by default, or with the FP64 kernel).
+// double-FP32 arithmetic, or with the FP64 kernel); by default only the first
+// residual of a solve is formed so, and the later ones are updated with the mixed
+// product of each (small) correction.
 //
 // The Krylov basis, the orthogonalisation (classical Gram-Schmidt applied
 // twice) and all vectors stay on the device in FP64; only the new Hessenberg
@@ -89,6 +91,12 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) y[i] += x[i];
+}
+
+__global__ void k_sub(double* __restrict__ y, const double* __restrict__ x, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] -= x[i];
 }
 
 inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -280,8 +288,21 @@ extern "C" int bem_solve(bem_ctx* c, int32_t precision, int32_t nrhs, const doub
             if (rc && rc != BEM_ERR_NOT_CONVERGED) return rc;
             k_axpy<<<nb(n), 256, 0, s>>>(x, d, n);
             BEM_LAUNCH_CHECK(c);
-            const int rprec = c->prm.residual == BEM_RESIDUAL_DF ? kPrecDF : BEM_FP64;
-            if ((rc = residual(c, rprec, c->bvec, x, ri))) return rc;
+            bool upd = false;
+            if (c->prm.residual == BEM_RESIDUAL_DF_UPDATE) {
+                double dn, xn;
+                if ((rc = norm2(c, d, &dn)) || (rc = norm2(c, x, &xn))) return rc;
+                upd = dn <= 1e-3 * xn;
+            }
+            if (upd) {
+                // b - A (x + d) = (b - A x) - A d: the correction's mixed product
+                if ((rc = apply(c, BEM_MIXED, false, d, c->rvec))) return rc;
+                k_sub<<<nb(n), 256, 0, s>>>(ri, c->rvec, n);
+                BEM_LAUNCH_CHECK(c);
+            } else {
+                const int rprec = c->prm.residual == BEM_RESIDUAL_FP64 ? BEM_FP64 : kPrecDF;
+                if ((rc = residual(c, rprec, c->bvec, x, ri))) return rc;
+            }
             if ((rc = norm2(c, ri, &rnorm))) return rc;
             if (total_iters >= c->prm.max_iters) break;
         }

@@ -53,7 +53,7 @@ int launch(bem_ctx* c, const TArgs& A, int64_t L, const double* seeds, double* K
     case G: {                                                                                    \
         constexpr size_t fsm = field_smem<F32, QQ>();                                            \
         BEM_CUDA_TRY(c, allow_smem(k_trace<F32, QQ>, fsm));                                      \
-        const int ncl = tracer_cluster(c->np);                                                   \
+        const int ncl = tracer_cluster(c->np, L, c->num_sms, c->prm.trace_cluster);             \
         const unsigned grid = lines_grid(k_trace<F32, QQ>, fsm, c->num_sms, L, ncl);             \
         BEM_CUDA_TRY(c, launch_lines(k_trace<F32, QQ>, grid, fsm, c->stream, ncl, A, seeds, L,   \
                                      c->d_line_next, K, st, ns, xe));                            \

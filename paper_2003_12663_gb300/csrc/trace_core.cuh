@@ -19,13 +19,15 @@
 // (at most 100 iterations); a step holds at most 4 events, the whole line at most
 // max_steps steps, so every loop is bounded.  Warps synchronise through CTA
 // barriers that every warp reaches once per round (a warp without a line joins
-// the rounds until no warp has one).  On meshes of kSplitMin triangles or more the
-// launch is made of clusters of two CTAs: the leader runs the lines, the helper
-// sweeps the second half of the triangles in every round of its leader, and the two
+// the rounds until no warp has one).  On meshes of kSplitMin triangles or more a
+// launch may be made of clusters of up to kCl CTAs: the leader runs the lines, each
+// helper sweeps its own part of the triangles in every round of its leader, and all
 // meet at the hardware cluster barrier twice per round (the round's points pushed
-// into the helper's shared memory, the helper's partial sums pushed into the
-// leader's).  Both run the same fixed sequence of barriers, paired one to one, and
-// no CTA waits on a CTA outside its own cluster.
+// into the helpers' shared memory; then the leader reads each helper's partial sums
+// from the helper's shared memory, in rank order).  Every CTA of a cluster runs the
+// same fixed sequence of barriers, paired one to one, and no CTA waits on a CTA
+// outside its own cluster.  The sums are grouped by the cluster's parts, so on such
+// meshes launches of different cluster sizes agree to rounding, not bit for bit.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -43,8 +45,9 @@ constexpr int kT = 256;          // threads of the adjoint's CTA-wide passes
 constexpr int kWarps = kT / 32;
 constexpr int kLW = 8;           // lines in flight per tracer CTA, one per warp
 constexpr int kLT = 32 * kLW;    // threads per tracer CTA
-constexpr int kCl = 2;           // largest tracer cluster: the leader and its helper
-constexpr int64_t kSplitMin = 8192;  // meshes of this many triangles or more are split over a cluster
+constexpr int kCl = 8;           // largest tracer cluster (the portable limit)
+constexpr int64_t kSplitMin = 8192;  // meshes of this many triangles or more may be split over a cluster
+constexpr int64_t kPartMin = 2048;   // an automatic split leaves every CTA at least this many triangles
 
 struct TArgs {
     int64_t np;
@@ -97,12 +100,12 @@ struct Round {
     double G[kLW][kLW][4];  // [target][warp] FP64 regular pairs (times 4 pi)
     int32_t near[kLW][kLW][kNearCap];  // [warp][target slot] triangles of near pairs found
     // cluster exchange: the leader pushes x, sr, act, args and exit into each helper's
-    // round; each helper pushes its partial sums into the leader's HF, HN, HG
+    // round; a helper leaves its part of the field at each posted point in P (sums over
+    // its warps in order: FP32 regular, closed-form, FP64 regular pairs, 4 components
+    // each), which the leader reads after the round's second cluster barrier
     TArgs args;
     int exit;
-    float HF[kCl - 1][kLW][kLW][4];
-    double HN[kCl - 1][kLW][kLW][4];
-    double HG[kCl - 1][kLW][kLW][4];
+    double P[kLW][12];
 };
 
 // the triangles [j0, j1) that the cluster's CTA of this rank sweeps in every round:
@@ -117,8 +120,26 @@ __device__ __forceinline__ void rank_range(int64_t np, int rank, int ncl, int64_
     j1 = min(np, j0 + per);
 }
 
-// cluster size of a tracer launch over meshes of at most np triangles
-inline int tracer_cluster(int64_t np) { return np >= kSplitMin ? kCl : 1; }
+// cluster size of a tracer launch over meshes of at most np triangles and `lines`
+// lines, on a GPU of num_sms SMs (one tracer CTA per SM): `want` (1..kCl) if given;
+// else the largest size that still leaves every CTA kPartMin triangles and whose
+// clusters, a GPU full of them with kLW lines each, hold at least a quarter of the
+// lines at once -- few lines get wide clusters (the rounds of a lone line, and the
+// tail of every run, are swept by several SMs), many lines plain CTAs (no exchange;
+// every SM is already busy with lines)
+inline int tracer_cluster(int64_t np, int64_t lines, int num_sms, int want = 0)
+{
+    if (want > 0) return std::min(want, kCl);
+    if (np < kSplitMin) return 1;
+    int ncl = 1;
+    for (int c = 2; c <= kCl; ++c) {
+        if (np / c < kPartMin) break;
+        const int64_t clusters = std::max(1, num_sms / c);
+        if (lines > 4 * clusters * kLW) break;
+        ncl = c;
+    }
+    return ncl;
+}
 
 // The FP32 evaluation streams the triangles through shared memory in chunks of TC
 // (nodes, classification header, normal + region, density) with an NS-stage ring of
@@ -415,7 +436,7 @@ __device__ __noinline__ void sweep(const TArgs& A, Round& R, int64_t j0, int64_t
 // entry barrier, with at least one point posted): push the posted points and the
 // arguments into every helper's round, meet the helpers at the cluster barrier,
 // sweep the leader's part of the triangles, and meet them again -- by then every
-// helper has pushed its partial sums into R.HF, R.HN, R.HG.
+// helper has left its part in its own R.P.
 template <bool F32, int Q>
 __device__ void eval_round(const TArgs& A, Round& R)
 {
@@ -451,15 +472,17 @@ __device__ __forceinline__ void release_helpers(Round& R)
 
 // A helper CTA (cluster rank >= 1): one iteration per round of its leader -- wait for
 // the pushed round, sweep this rank's part of the triangles for the posted points,
-// push the partial sums into the leader's round, meet the leader again.  Its barriers
-// pair one to one with the leader's (two per round, one at the release), so the two
-// CTAs go through the same sequence of cluster barriers.  A CTA only writes the
-// other's shared memory and reads its own.
+// sum the warps' partial sums into R.P, meet the leader again.  Its barriers pair one
+// to one with the leader's (two per round, one at the release), so every CTA of the
+// cluster goes through the same sequence of cluster barriers.  The leader writes a
+// helper's x, sr, act, args and exit only between the helper's second barrier of a
+// round and its first of the next (the helper reads them after that one), and reads
+// a helper's P only between those two barriers too (the helper writes it before the
+// second), so no access races.
 template <bool F32, int Q>
 __device__ void helper_rounds(Round& R, int rank)
 {
     cg::cluster_group cl = cg::this_cluster();
-    Round* R0 = cl.map_shared_rank(&R, 0);
     for (;;) {
         cl.sync();                    // the leader has pushed a round, or the release
         if (R.exit) break;
@@ -467,14 +490,15 @@ __device__ void helper_rounds(Round& R, int rank)
         rank_range(R.args.np, rank, (int)cl.num_blocks(), j0, j1);
         sweep<F32, Q>(R.args, R, j0, j1);
         cta_bar();                    // every warp's partial sums are in R
-        for (int i = threadIdx.x; i < kLW * kLW * 4; i += kLT) {
-            const int k = i / (kLW * 4), w = (i / 4) % kLW, c = i % 4;
+        for (int i = threadIdx.x; i < kLW * 12; i += kLT) {
+            const int k = i / 12, a = (i % 12) / 4, c = i % 4;
             if (!R.act[k]) continue;
-            R0->HF[rank - 1][k][w][c] = R.F[k][w][c];
-            R0->HN[rank - 1][k][w][c] = R.N[k][w][c];
-            R0->HG[rank - 1][k][w][c] = R.G[k][w][c];
+            double v = 0.0;
+#pragma unroll
+            for (int u = 0; u < kLW; ++u) v += a == 0 ? (double)R.F[k][u][c] : (a == 1 ? R.N[k][u][c] : R.G[k][u][c]);
+            R.P[k][i % 12] = v;
         }
-        cl.sync();                    // the leader may read them
+        cl.sync();                    // the leader may read R.P
     }
 }
 
@@ -490,11 +514,10 @@ __device__ __forceinline__ V4 round_result(const Round& R, int w)
 #pragma unroll
     for (int u = 0; u < kLW; ++u)
         v += a == 0 ? (double)R.F[w][u][c] : (a == 1 ? R.N[w][u][c] : R.G[w][u][c]);
-    // the helper's part (a cluster of two)
-    if (cg::this_cluster().num_blocks() > 1)
-#pragma unroll
-        for (int u = 0; u < kLW; ++u)
-            v += a == 0 ? (double)R.HF[0][w][u][c] : (a == 1 ? R.HN[0][w][u][c] : R.HG[0][w][u][c]);
+    // the helpers' parts, in rank order
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncl = (int)cl.num_blocks();
+    for (int h = 1; h < ncl; ++h) v += cl.map_shared_rank(&R, h)->P[w][4 * a + c];
     double f[4], n[4], g[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -820,18 +843,37 @@ __device__ void run_lines(ArgsFn args, CountFn L, int ninst, int64_t total, unsi
     release_helpers(R);
 }
 
-// persistent grid of a tracer kernel, in whole clusters: every resident CTA slot of
-// the GPU, but never more clusters than lines (with the per-cluster cap of run_lines,
+// persistent grid of a tracer kernel, in whole clusters: as many clusters as the GPU
+// holds at once (a cluster must fit in one GPC, so wide clusters may leave SMs
+// over), but never more clusters than lines (with the per-cluster cap of run_lines,
 // few lines spread one per cluster, many lines fill every warp)
-template <class Kernel>
-inline unsigned lines_grid(Kernel k, size_t smem, int num_sms, int64_t lines, int ncl)
+template <class... KArgs>
+inline unsigned lines_grid(void (*k)(KArgs...), size_t smem, int num_sms, int64_t lines, int ncl)
 {
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kLT, smem) != cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;
     }
-    const int64_t clusters = (int64_t)num_sms * std::max(per_sm, 1) / ncl;
+    int64_t clusters = (int64_t)num_sms * std::max(per_sm, 1) / ncl;
+    if (ncl > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(ncl * clusters));
+        cfg.blockDim = dim3(kLT);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = ncl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) == cudaSuccess && nc > 0)
+            clusters = std::min<int64_t>(clusters, nc);
+        else
+            cudaGetLastError();
+    }
     return (unsigned)(ncl * std::max<int64_t>(1, std::min(clusters, lines)));
 }
 

@@ -143,6 +143,27 @@ def test_checkpoint_interval_and_line_chunks(bem):
         assert np.allclose(x, y, rtol=1e-12, atol=1e-15 * np.abs(x).max())
 
 
+def test_checkpoints_on_split_mesh(bem):
+    """On a mesh whose tracer rounds are split over a cluster (9,834 triangles, clusters
+    of 3 CTAs), the recomputed segments retrace the forward pass bit for bit: every
+    checkpoint interval gives the same gradient, and K is bem_trace_lines' K."""
+    mesh = mg.device_mesh(0.7, seed=2)
+    seeds = np.array([[0.1, 0.05, 1.0], [-0.2, 0.1, 1.0]])  # above the sphere: lines reach r_max
+    seeds = 1.05 * seeds / np.linalg.norm(seeds, axis=1, keepdims=True)
+    w = np.array([0.7, 1.3])
+    a = _gpu_adjoint(bem, mesh, seeds, w, bem.MIXED, trace_cluster=3, adjoint_checkpoint=128)
+    b = _gpu_adjoint(bem, mesh, seeds, w, bem.MIXED, trace_cluster=3, adjoint_checkpoint=7)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    ctx = bem.Context(mesh, trace_cluster=3)
+    u, _, _ = ctx.solve(bem.MIXED, tol=1e-10)
+    K, st, _, _ = ctx.trace_lines(u[0], torch.tensor(seeds), bem.MIXED, h=H)
+    ctx.close()
+    assert np.all(st.cpu().numpy() == 1)
+    assert np.allclose(a[0], K.cpu().numpy(), rtol=1e-13, atol=0)
+    assert np.abs(a[1]).max() > 0
+
+
 def test_no_workspace(bem):
     mesh = mg.sphere_mesh(1)
     ctx = bem.Context(mesh, adjoint_lines=0)

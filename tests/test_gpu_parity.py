@@ -132,10 +132,12 @@ def test_matvec_df_multi_rhs(case, bem, nr):
         assert np.abs(Y[r].cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-11
 
 
-@pytest.mark.parametrize("residual", [0, 1])
+@pytest.mark.parametrize("residual", [0, 1, 2], ids=["df", "fp64", "df_update"])
 def test_mixed_solve_residual_modes(case, bem, residual):
-    """BEM_MIXED with the refinement residual in double-FP32 (default) or FP64:
-    the FP64 residual of the result meets the tolerance and sigma matches LU."""
+    """BEM_MIXED with every refinement residual in double-FP32 or FP64, or (the
+    default) the first in double-FP32 and the later ones updated with the mixed product
+    of the correction: the FP64 residual of the result meets the tolerance and sigma
+    matches LU."""
     name, mesh, ctx, P, A = case
     c2 = bem.Context(mesh, residual=residual)
     u, iters, rel = c2.solve(bem.MIXED, tol=1e-10)

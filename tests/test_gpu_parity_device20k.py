@@ -142,3 +142,68 @@ def test_row_block(bem, dev20k, ctx20k, prec, tol, body):
     A = ctx20k.assemble_rows(r0, r1, precision=prec).cpu().numpy()
     scale = np.abs(ref).max(axis=1, keepdims=True)
     assert np.max(np.abs(A - ref) / scale) < tol
+
+
+def test_refinement_residual_update(bem, dev20k):
+    """The default refinement forms one double-FP32 residual per solve and updates the
+    later ones with the mixed product of the correction: on the 20k device the true
+    residual of the result (FP64 product) still meets the tolerance, and the solution
+    is the every-step double-FP32 one to 1e-6."""
+    mesh = dev20k[0]
+    out = {}
+    for mode in (bem.RESIDUAL_DF_UPDATE, bem.RESIDUAL_DF):
+        ctx = bem.Context(mesh, residual=mode)
+        ctx.reset_counters()
+        u, iters, rel = ctx.solve(bem.MIXED, tol=1e-8)
+        c = ctx.counters()
+        b = ctx.rhs()[0]
+        r = (b - ctx.matvec(u[0], precision=bem.FP64)).norm() / b.norm()
+        out[mode] = (u[0].cpu().numpy(), r.item(), rel[0], c["matvecs"][bem.DF])
+        ctx.close()
+    uu, ru, relu, ndf_u = out[bem.RESIDUAL_DF_UPDATE]
+    ud, rd, reld, ndf_d = out[bem.RESIDUAL_DF]
+    assert ru <= 1.05e-8 and abs(ru - relu) <= 5e-10, (ru, relu)
+    assert rd <= 1.05e-8
+    assert ndf_u == 1 and ndf_d >= 2, (ndf_u, ndf_d)
+    assert np.linalg.norm(uu - ud) / np.linalg.norm(ud) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def many_points(oracle_mod, dev20k):
+    """12,288 points in random order (uniform box points, a tight cluster and points
+    1e-4 off the surface), with the oracle's field: chunks this large are evaluated in
+    spatial order by the packed kernel."""
+    mesh, P, x = dev20k[0], dev20k[1], dev20k[2]
+    rng = np.random.default_rng(77)
+    pts = np.concatenate([mg.device_box_points(10240, seed=56), dev20k[4][:1024],
+                          P.centroids[::20][:1024] + 1e-4 * P.normals[::20][:1024]])
+    pts = pts[rng.permutation(len(pts))]
+    phi_r, E_r = P.field(x, pts)
+    return pts, phi_r, E_r
+
+
+@pytest.mark.parametrize("variant", [2, 4], ids=lambda v: f"far32v{v}")
+def test_field_in_spatial_order(bem, dev20k, many_points, variant):
+    """bem_eval_field sorts each chunk of at least 4,096 points by cell of a 16^3 grid
+    along the Morton curve before the packed kernel: the field matches the oracle
+    (1e-5 of max|phi|, max|E|), most triangle chunks are then summed unmasked, and the
+    result is the unordered evaluation's (chunks of 4,095 points) to FP32 rounding."""
+    x = dev20k[2]
+    pts, phi_r, E_r = many_points
+    ctx = bem.Context(dev20k[0], far32_variant=variant)
+    ctx.reset_counters()
+    phi, E = ctx.eval_field(torch.tensor(x), torch.tensor(pts), precision=bem.MIXED)
+    c = ctx.counters()
+    ctx.close()
+    phi, E = phi.cpu().numpy(), E.cpu().numpy()
+    assert _rel(phi, phi_r) < 1e-5
+    assert _rel(E, E_r) < 1e-5
+    assert c["fast_chunks32p"] > 0.5 * c["chunks32p"], c
+    small = bem.Context(dev20k[0], far32_variant=variant, max_points=4095)
+    small.reset_counters()
+    phi2, E2 = small.eval_field(torch.tensor(x), torch.tensor(pts), precision=bem.MIXED)
+    c2 = small.counters()
+    small.close()
+    assert c2["fast_chunks32p"] < c["fast_chunks32p"], (c, c2)
+    assert _rel(phi2.cpu().numpy(), phi) < 2e-6
+    assert _rel(E2.cpu().numpy(), E) < 2e-6

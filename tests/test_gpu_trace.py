@@ -102,3 +102,57 @@ def test_trace_second_electrode(oracle_mod):
     assert np.array_equal(ns, nso)
     assert np.abs(K - Ko).max() < 1e-9 and np.abs(xe - xeo).max() < 1e-9
     ctx.close()
+
+
+@pytest.fixture(scope="module")
+def device_split(oracle_mod):
+    """The multi-domain device at 9,834 triangles: large enough for the tracer to split
+    every round's triangles over the CTAs of a cluster."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2003_12663_gb300 import bem
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mesh = mg.device_mesh(0.7, seed=2)
+    assert mesh.tri.shape[0] >= 8192
+    ctx = bem.Context(mesh)
+    u, _, _ = ctx.solve(bem.FP64, tol=1e-12)
+    ctx.close()
+    seeds = mg.fibonacci_seeds(64, radius=1.05)[3::16]
+    P = oracle_mod.Problem(mesh, eta=4.0, g=3)
+    ref = P.trace(u[0].cpu().numpy(), seeds, oracle_mod.TraceParams(h=0.01))
+    return bem, mesh, u[0], seeds, ref
+
+
+@pytest.mark.parametrize("ncl", [1, 2, 3, 8])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_trace_cluster_split_matches_oracle(device_split, prec, ncl):
+    """Clusters of 1, 2, 3 and 8 CTAs (the triangles of every round split into ncl
+    parts, the last of them ragged) trace the oracle's lines: FP64 to rounding with the
+    same statuses and step counts, mixed to the FP32 error of the field."""
+    bem, mesh, u, seeds, (Ko, sto, nso, xeo) = device_split
+    ctx = bem.Context(mesh, trace_cluster=ncl)
+    K, st, ns, xe = (a.cpu().numpy() for a in ctx.trace_lines(u, torch.tensor(seeds), prec, h=0.01))
+    ctx.close()
+    assert np.array_equal(st, sto) and np.all(st > 0)
+    if prec == 0:
+        assert np.array_equal(ns, nso)
+        assert np.abs(K - Ko).max() < 1e-9 * np.abs(Ko).max()
+        assert np.abs(xe - xeo).max() < 1e-9
+    else:
+        assert np.abs(ns - nso).max() <= 1
+        assert np.abs(K - Ko).max() < 1e-5 * np.abs(Ko).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_trace_cluster_split_bitwise(device_split, prec):
+    """With the same cluster size, the batched tracer gives bem_trace_lines' results bit
+    for bit on a split mesh too."""
+    bem, mesh, u, seeds, _ = device_split
+    ctx = bem.Context(mesh, trace_cluster=4)
+    K1, s1, n1, _ = ctx.trace_lines(u, torch.tensor(seeds), prec, h=0.01)
+    B = bem.Batch([ctx], nrhs=1)
+    K, st, ns = B.trace([u], [seeds], prec, h=0.01)
+    assert torch.equal(K[0], K1) and torch.equal(st[0], s1) and torch.equal(ns[0], n1)
+    B.close()
+    ctx.close()
