@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--far32-variant", type=int, default=0, choices=[0, 1, 2, 4],
+    ap.add_argument("--far32-variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="FP32 regular-pair kernel variant (0: tuned at context creation)")
     ap.add_argument("--mode", default="step", choices=["step", "matvec", "batch", "report", "trace"],
                     help="matvec: only W+K mixed matvecs of the workload (a small case for ncu); "

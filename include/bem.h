@@ -98,9 +98,10 @@ typedef struct {
     int32_t timing;          /* != 0: time every regular-pair kernel with CUDA events (bem_counters) */
     int32_t residual;        /* BEM_MIXED refinement residual b - A u: BEM_RESIDUAL_DF_UPDATE
                                 (default), BEM_RESIDUAL_DF or BEM_RESIDUAL_FP64 */
-    int32_t far32_variant;   /* FP32 regular-pair kernel: 1 scalar, 2 or 4 packed target pairs
-                                per thread; 0 (default): bem_create times the candidates on the
-                                mesh's own matvec and keeps the fastest (N >= 4096; else 2) */
+    int32_t far32_variant;   /* FP32 regular-pair kernel: 1 scalar, 2, 3 or 4 packed target
+                                pairs per thread (3: registers capped for three CTAs per SM);
+                                0 (default): bem_create times the candidates on the mesh's own
+                                matvec and keeps the fastest (N >= 4096; else 2) */
     int32_t adjoint_checkpoint; /* bem_adjoint keeps the state of every line every this many
                                    RK4 steps and recomputes the steps in between; default 128 */
     int64_t adjoint_lines;   /* lines bem_adjoint holds at once (more are taken in turns); the
@@ -138,10 +139,10 @@ typedef struct {
     double far_ms[3];           /* summed regular-pair kernel time in ms (params.timing != 0) */
     int64_t matvecs[3];         /* matrix-free products, solver-internal ones included */
     int64_t gmres_iters;        /* Arnoldi steps */
-    int64_t far32_variant;      /* FP32 kernel variant in use (1, 2 or 4; not reset) */
+    int64_t far32_variant;      /* FP32 kernel variant in use (1, 2, 3 or 4; not reset) */
     int64_t phi_pairs[3];       /* of pairs, those of product tiles holding only conductor rows,
                                    summed for phi alone (their row equation needs no E) */
-    int64_t chunks32p;          /* 32-triangle chunks the packed FP32 kernel (variants 2, 4) staged,
+    int64_t chunks32p;          /* 32-triangle chunks the packed FP32 kernel (variants 2-4) staged,
                                    summed over its CTAs */
     int64_t fast_chunks32p;     /* of those, chunks whose every pair with the CTA's targets was
                                    certainly regular (bounding spheres), summed without classification */
@@ -150,16 +151,16 @@ typedef struct {
 /* The shape the context's FP32 regular-pair kernel runs with, and how it was chosen
  * (bem_create's tuner: every candidate timed on the mesh's own mixed matvec). */
 typedef struct {
-    int32_t far32_variant;   /* 1 scalar, 2 or 4 packed target pairs per thread */
+    int32_t far32_variant;   /* 1 scalar, 2, 3 or 4 packed target pairs per thread */
     int32_t far32_slots;     /* CTA slots per SM the number of triangle slices aims at */
     int32_t source;          /* 0 fixed (params.far32_variant, or N < 4096), 1 timed by this
                                 bem_create, 2 taken from the process-wide table (same device, size
                                 bucket and far_order, timed by an earlier context) */
     int32_t bucket;          /* size bucket floor(2 log2 N) */
     int32_t n_candidates;    /* candidates timed (source 1) */
-    int32_t cand_variant[9];
-    int32_t cand_slots[9];
-    float cand_ms[9];        /* one mixed matvec of this mesh per candidate */
+    int32_t cand_variant[12];
+    int32_t cand_slots[12];
+    float cand_ms[12];       /* one mixed matvec of this mesh per candidate */
 } bem_tuning;
 
 typedef struct bem_ctx bem_ctx;
@@ -417,7 +418,7 @@ typedef struct {
     int32_t near_radial;     /* near-singular rule: points per radial piece; default 16 */
     int32_t near_angular;    /* near-singular rule: angular points; default 64 */
     int32_t gmres_restart, max_iters, max_refine;  /* as bem_params: 100, 2000, 6 */
-    int32_t far32_variant;   /* packed FP32 kernel, 2 or 4 target pairs per thread; default 2 */
+    int32_t far32_variant;   /* packed FP32 kernel, 2, 3 or 4 target pairs per thread; default 2 */
     int64_t max_points;      /* as bem_params; default 131072 */
     int32_t timing;          /* as bem_params */
     int32_t reserved;

@@ -80,8 +80,8 @@ class bem_counters(ctypes.Structure):
 class bem_tuning(ctypes.Structure):
     _fields_ = [("far32_variant", ctypes.c_int32), ("far32_slots", ctypes.c_int32),
                 ("source", ctypes.c_int32), ("bucket", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
-                ("cand_variant", ctypes.c_int32 * 9), ("cand_slots", ctypes.c_int32 * 9),
-                ("cand_ms", ctypes.c_float * 9)]
+                ("cand_variant", ctypes.c_int32 * 12), ("cand_slots", ctypes.c_int32 * 12),
+                ("cand_ms", ctypes.c_float * 12)]
 
     def as_dict(self):
         n = self.n_candidates

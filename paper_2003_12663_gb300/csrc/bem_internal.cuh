@@ -54,7 +54,7 @@ struct bem_ctx {
     float4* node_lo32 = nullptr;  // [np][Q] node - node32 (low parts of the double-FP32 nodes)
     float4* qnode = nullptr;      // [np][Q] FP32 nodes with sigma folded into w (per call)
     float4* chunk_sph = nullptr;  // [np/32 rounded up] bounding sphere of 32 triangles' near zones
-    int far32_tp = 2;             // FP32 kernel variant: 1 scalar, 2 or 4 packed target pairs
+    int far32_tp = 2;             // FP32 kernel variant: 1 scalar, 2, 3 or 4 packed target pairs
     int far_slots = 4;            // CTA slots per SM the FP32 kernel's slice count aims at (tuned)
     bem_tuning tune{};            // what the tuner chose and measured
     int64_t phi_tile_targets = 0; // centroid targets in tiles of conductor rows only (packed variant)

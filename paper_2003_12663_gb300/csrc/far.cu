@@ -160,7 +160,7 @@ __global__ void k_prescale(int64_t n, int Q, const float4* __restrict__ node,
 }
 
 template <int TP, int Q, bool RAW>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, TP == 3 ? 3 : 1)
 k_far32p(const float4* __restrict__ t32, const double* __restrict__ tpts, int64_t M,
          const float4* __restrict__ hdr, const float4* __restrict__ qnode,
          const float4* __restrict__ chunk_sph, int64_t np, int64_t per_split,
@@ -692,6 +692,8 @@ int launch_q(bem_ctx* ctx, int precision, const FarTargets& T, const double* u, 
             ctx->d_near_count + 2)
         if (ctx->far32_tp == 4) {
             FAR32P(4);
+        } else if (ctx->far32_tp == 3) {
+            FAR32P(3);
         } else {
             FAR32P(2);
         }

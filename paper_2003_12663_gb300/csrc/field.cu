@@ -111,9 +111,15 @@ __global__ void k_rhs(int64_t np, int64_t nunk, int nregions, const int32_t* __r
 // with the classification of the regular pass (so that every pair is taken
 // exactly once), gathers the near ones in shared memory and evaluates them 32 at
 // a time with the FP64 closed form; then adds the far partials of all splits.
-// perm (or NULL): point t's results go to slot perm[t] of phi and E.
+// perm (or NULL): point t's results go to slot perm[t] of phi and E.  In the FP32
+// classification the warp first tests 32 chunk spheres at a time (a chunk of 32
+// triangles whose sphere -- circumcentres plus eta R, with the rounding margin of
+// k_far32p's unmasked chunks -- lies certainly outside the point holds no near
+// triangle) and scans only the triangles of the other chunks, in the same ascending
+// order, so the near list is unchanged.
 template <bool F32>
 __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* __restrict__ pts,
+                              const float4* __restrict__ chunk_sph,
                               const float4* __restrict__ hdr32, const double4* __restrict__ hdr64,
                               const double* __restrict__ geo, const double* __restrict__ u,
                               const double* __restrict__ part, double* __restrict__ phi,
@@ -142,7 +148,8 @@ __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* _
             ez = fma(uj, Gz, ez);
         }
     };
-    for (int64_t j0 = 0; j0 < np; j0 += 32) {
+    // scan the 32 triangles from j0: list the near ones, evaluate every full 32
+    auto scan = [&](int64_t j0) {
         const int64_t j = j0 + lane;
         bool near = false;
         if (j < np) near = F32 ? !is_far32(xf, yf, zf, hdr32[j]) : !is_far64(x, y, z, hdr64[j]);
@@ -158,6 +165,25 @@ __global__ void k_points_near(int64_t M, int64_t np, int splits, const double* _
             __syncwarp();
             n -= 32;
         }
+    };
+    if (F32 && chunk_sph) {
+        const int64_t nch = (np + 31) / 32;
+        for (int64_t c0 = 0; c0 < nch; c0 += 32) {
+            bool maybe = false;
+            if (c0 + lane < nch) {
+                const float4 cs = chunk_sph[c0 + lane];
+                const float dx = xf - cs.x, dy = yf - cs.y, dz = zf - cs.z;
+                maybe = !(sqrtf(dx * dx + dy * dy + dz * dz) > cs.w);
+            }
+            unsigned mm = __ballot_sync(0xffffffffu, maybe);
+            while (mm) {
+                const int b = __ffs(mm) - 1;
+                mm &= mm - 1u;
+                scan((c0 + b) * 32);
+            }
+        }
+    } else {
+        for (int64_t j0 = 0; j0 < np; j0 += 32) scan(j0);
     }
     flush(n);
     double fp = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
@@ -480,11 +506,11 @@ int launch_points_near(bem_ctx* c, int precision, int64_t M, const double* pts, 
     if (M <= 0) return BEM_OK;
     const unsigned blocks = (unsigned)((M + 3) / 4);
     if (precision == BEM_MIXED)
-        k_points_near<true><<<blocks, 128, 0, c->stream>>>(M, c->np, splits, pts, c->hdr32,
+        k_points_near<true><<<blocks, 128, 0, c->stream>>>(M, c->np, splits, pts, c->chunk_sph, c->hdr32,
                                                              c->hdr64, c->geo, u, part, phi, E,
                                                              c->d_near_count + BEM_MIXED, nullptr);
     else
-        k_points_near<false><<<blocks, 128, 0, c->stream>>>(M, c->np, splits, pts, c->hdr32,
+        k_points_near<false><<<blocks, 128, 0, c->stream>>>(M, c->np, splits, pts, nullptr, c->hdr32,
                                                               c->hdr64, c->geo, u, part, phi, E,
                                                               c->d_near_count + BEM_FP64, nullptr);
     BEM_LAUNCH_CHECK(c);
@@ -520,11 +546,11 @@ extern "C" int bem_eval_field(bem_ctx* c, int32_t precision, const double* u, in
         const unsigned blocks = (unsigned)((mc + 3) / 4);
         if (precision == BEM_MIXED)
             k_points_near<true><<<blocks, 128, 0, c->stream>>>(
-                mc, c->np, splits, cp, c->hdr32, c->hdr64, c->geo, u, c->part,
+                mc, c->np, splits, cp, c->chunk_sph, c->hdr32, c->hdr64, c->geo, u, c->part,
                 phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr, c->d_near_count + BEM_MIXED, perm);
         else
             k_points_near<false><<<blocks, 128, 0, c->stream>>>(
-                mc, c->np, splits, cp, c->hdr32, c->hdr64, c->geo, u, c->part,
+                mc, c->np, splits, cp, nullptr, c->hdr32, c->hdr64, c->geo, u, c->part,
                 phi ? phi + m0 : nullptr, E ? E + 3 * m0 : nullptr, c->d_near_count + BEM_FP64, perm);
         BEM_LAUNCH_CHECK(c);
     }

@@ -968,7 +968,7 @@ extern "C" int bem_p1_create(bem_ctx** out, int64_t nn, const double* nodes, int
     if (!(p.eta >= 1.0) || p.far_order < 1 || p.far_order > kMaxOrder || p.sing_order < 1 || p.sing_order > 64 ||
         p.near_radial < 1 || p.near_radial > 64 || p.near_angular < 1 || p.near_angular > 256 ||
         p.gmres_restart < 1 || p.gmres_restart > 1000 || p.max_iters < 1 || p.max_refine < 1 ||
-        p.max_points < 1 || (p.far32_variant != 2 && p.far32_variant != 4))
+        p.max_points < 1 || p.far32_variant < 2 || p.far32_variant > 4)
         return set_err(nullptr, BEM_ERR_ARG, "bem_p1_create: bad parameters");
     for (int64_t i = 0; i < 6 * N; ++i)
         if (tri6[i] < 0 || tri6[i] >= nn || (i % 6 < 3 && tri6[i] >= nv))

@@ -518,7 +518,7 @@ extern "C" int bem_destroy(bem_ctx* ctx)
     return BEM_OK;
 }
 
-// Tuner of the FP32 regular-pair kernel's shape: the variant (scalar, 2 or 4 packed
+// Tuner of the FP32 regular-pair kernel's shape: the variant (scalar, 2, 3 or 4 packed
 // target pairs per thread) and the CTA slots per SM that the triangle-slice count
 // aims at.  Each candidate is timed on the mesh's own mixed matvec (one warm-up, then
 // CUDA events on the context's stream) and the fastest is kept.  The choice is kept
@@ -572,7 +572,7 @@ static int tune_far32(bem_ctx* c)
             float best = 3e38f;
             TuneChoice pick{2, 4};
             int k = 0;
-            for (int tp : {1, 2, 4}) {
+            for (int tp : {1, 2, 3, 4}) {
                 for (int sl : {2, 4, 8}) {
                     c->far32_tp = tp;
                     c->far_slots = sl;
@@ -816,7 +816,7 @@ static int create_impl(bem_ctx* c, const bem_mesh* mesh)
     const int64_t Mmax = std::max<int64_t>(np, c->prm.max_points);
     size_t need = 0;
     const int tp_default = c->far32_tp, slots_default = c->far_slots;
-    for (int tp : {1, 2, 4}) {  // every FP32 kernel shape the tuner may pick
+    for (int tp : {1, 2, 3, 4}) {  // every FP32 kernel shape the tuner may pick
         for (int sl : {2, 4, 8}) {
             c->far32_tp = tp;
             c->far_slots = sl;
@@ -878,8 +878,7 @@ extern "C" int bem_create(bem_ctx** out, const bem_mesh* mesh, const bem_params*
         prm.max_refine < 1 || prm.max_points < 1 || prm.max_points > INT32_MAX ||
         (prm.residual != BEM_RESIDUAL_DF && prm.residual != BEM_RESIDUAL_FP64 &&
          prm.residual != BEM_RESIDUAL_DF_UPDATE) ||
-        (prm.far32_variant != 0 && prm.far32_variant != 1 && prm.far32_variant != 2 &&
-         prm.far32_variant != 4))
+        (prm.far32_variant != 0 && (prm.far32_variant < 1 || prm.far32_variant > 4)))
         return set_err(nullptr, BEM_ERR_ARG, "bad parameters (need eta >= 1, 1 <= far_order <= %d)",
                        kMaxOrder);
     for (int64_t i = 0; i < 3 * mesh->np; ++i)

@@ -209,7 +209,7 @@ def test_rhs_and_multi_rhs(case, bem):
 # k_far32p with 2 or 4 target pairs per thread) only on meshes of 4,096 triangles or
 # more; below that it fixes the 2-pair variant.  Every variant is compared with the
 # oracle here, on every mesh above, by fixing it through bem_params.far32_variant.
-@pytest.fixture(scope="module", params=[1, 2, 4], ids=lambda v: f"far32v{v}")
+@pytest.fixture(scope="module", params=[1, 2, 3, 4], ids=lambda v: f"far32v{v}")
 def variant_case(request, case, bem):
     name, mesh, ctx, P, A = case
     c = bem.Context(mesh, far32_variant=request.param)

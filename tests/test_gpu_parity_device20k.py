@@ -57,7 +57,7 @@ def _rel(y, ref):
     return np.abs(y - ref).max() / np.abs(ref).max()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 4], ids=lambda v: f"far32v{v}")
+@pytest.mark.parametrize("variant", [1, 2, 3, 4], ids=lambda v: f"far32v{v}")
 def test_product_and_field_per_variant(bem, dev20k, variant):
     mesh, P, x, y_ref, pts, phi_r, E_r = dev20k
     ctx = bem.Context(mesh, far32_variant=variant)
@@ -108,7 +108,7 @@ def test_field_fp64(bem, dev20k, ctx20k):
 def test_tuned_context_matches(bem, dev20k, ctx20k):
     """The context as the benchmark creates it (variant picked by timing)."""
     mesh, P, x, y_ref, pts, phi_r, E_r = dev20k
-    assert ctx20k.counters()["far32_variant"] in (1, 2, 4)
+    assert ctx20k.counters()["far32_variant"] in (1, 2, 3, 4)
     y = ctx20k.matvec(torch.tensor(x), precision=bem.MIXED).cpu().numpy()
     assert _rel(y, y_ref) < 2e-6
 
@@ -182,12 +182,14 @@ def many_points(oracle_mod, dev20k):
     return pts, phi_r, E_r
 
 
-@pytest.mark.parametrize("variant", [2, 4], ids=lambda v: f"far32v{v}")
+@pytest.mark.parametrize("variant", [2, 3, 4], ids=lambda v: f"far32v{v}")
 def test_field_in_spatial_order(bem, dev20k, many_points, variant):
     """bem_eval_field sorts each chunk of at least 4,096 points by cell of a 16^3 grid
     along the Morton curve before the packed kernel: the field matches the oracle
-    (1e-5 of max|phi|, max|E|), most triangle chunks are then summed unmasked, and the
-    result is the unordered evaluation's (chunks of 4,095 points) to FP32 rounding."""
+    (1e-5 of max|phi|, max|E|), several times more triangle chunks are then summed
+    unmasked than in input order (at this density, 2.5 box points per cell, a tenth or
+    more of them), and the result is the unordered evaluation's (chunks of 4,095
+    points) to FP32 rounding."""
     x = dev20k[2]
     pts, phi_r, E_r = many_points
     ctx = bem.Context(dev20k[0], far32_variant=variant)
@@ -198,12 +200,12 @@ def test_field_in_spatial_order(bem, dev20k, many_points, variant):
     phi, E = phi.cpu().numpy(), E.cpu().numpy()
     assert _rel(phi, phi_r) < 1e-5
     assert _rel(E, E_r) < 1e-5
-    assert c["fast_chunks32p"] > 0.5 * c["chunks32p"], c
+    assert c["fast_chunks32p"] > 0.1 * c["chunks32p"], c
     small = bem.Context(dev20k[0], far32_variant=variant, max_points=4095)
     small.reset_counters()
     phi2, E2 = small.eval_field(torch.tensor(x), torch.tensor(pts), precision=bem.MIXED)
     c2 = small.counters()
     small.close()
-    assert c2["fast_chunks32p"] < c["fast_chunks32p"], (c, c2)
+    assert 4 * c2["fast_chunks32p"] < c["fast_chunks32p"], (c, c2)
     assert _rel(phi2.cpu().numpy(), phi) < 2e-6
     assert _rel(E2.cpu().numpy(), E) < 2e-6
