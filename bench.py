@@ -505,6 +505,28 @@ def fp64_form(args, bem, ctx, mesh, pts_d, out, cnt, ms_mixed, stream, flush):
             "E_rel_mixed_vs_fp64_on_sample": dE}
 
 
+def p1_vertex_weights(nodes, tri6, nv, body, nbody, g=8):
+    """w[b, v] = integral of the linear basis function of vertex v over the curved
+    six-node triangles of body b: a g x g Gauss rule on the square mapped onto each
+    triangle (xi = s(1 - t), eta = s t, Jacobian s), times the area element
+    |dy/dxi x dy/deta| of the quadratic map."""
+    x, wx = np.polynomial.legendre.leggauss(g)
+    x, wx = 0.5 * (x + 1.0), 0.5 * wx
+    s, t = np.meshgrid(x, x, indexing="ij")
+    ws = (wx[:, None] * wx[None, :] * s).ravel()
+    xi, eta = (s * (1.0 - t)).ravel(), (s * t).ravel()
+    l0 = 1.0 - xi - eta
+    dxi = np.stack([1.0 - 4.0 * l0, 4.0 * xi - 1.0, 0.0 * xi, 4.0 * (l0 - xi), 4.0 * eta, -4.0 * eta], 1)
+    deta = np.stack([1.0 - 4.0 * l0, 0.0 * xi, 4.0 * eta - 1.0, -4.0 * xi, 4.0 * xi, 4.0 * (l0 - eta)], 1)
+    lam = np.stack([l0, xi, eta], 1)
+    out = np.zeros((nbody, nv))
+    for T in range(len(tri6)):
+        P = nodes[tri6[T]]
+        J = np.linalg.norm(np.cross(dxi @ P, deta @ P), axis=1)
+        np.add.at(out[body[T]], tri6[T, :3], (ws * J) @ lam)
+    return out
+
+
 def trace_block(args, bem):
     """Field lines beside the step (untimed by the step's clock, CUDA events of their own):
     c3's 256 Fibonacci lines on the 1,280-triangle sphere (h = 1e-3, r_max = 10), and
@@ -995,6 +1017,26 @@ def run_report(args):
             emit({"config": f"curved sphere level {level}: {len(tri6)} six-node triangles, {nv} vertices, "
                             f"P1 collocation, V0=1, tol 1e-10",
                   "setup_ms": t_set, "near_pairs": ctx.near_pairs, **res})
+            ctx.close()
+        # a conductor inside a dielectric ball (Eq. Final3 rows): charges against Gauss's law
+        for level in (2, 3):
+            nodes, tri6, nv, body = mg.quadratic_bodies([mg.quadratic_sphere(level, 1.0),
+                                                         mg.quadratic_sphere(level, 2.0)])
+            body = np.asarray(body, np.int32)
+            regs = [{"kind": "conductor", "V0": 1.0}, {"kind": "dielectric", "eps_plus": 1.0, "eps_minus": 4.0}]
+            ctx, t_set = wall(lambda: bem.P1Context(nodes, tri6, nv, body, regs))
+            Qg = 4 * np.pi / (1.0 / 4.0 + 0.75 / 2.0)
+            want = np.array([Qg / 4.0, Qg * 0.75])
+            wts = p1_vertex_weights(nodes, tri6, nv, body, 2)   # int psi_v dS per body
+            res = {}
+            for name, prec in (("fp64", bem.FP64), ("mixed", bem.MIXED)):
+                (u, it, rel), t_sol = timed(lambda: ctx.solve(prec, tol=1e-10))
+                q = wts @ u[0].cpu().numpy()[:nv]
+                res[name] = {"solve_ms": t_sol, "iters": it, "relres": rel[0],
+                             "charge_rel_err_vs_gauss": [float(v) for v in np.abs(q - want) / want]}
+            emit({"config": f"curved conductor sphere (a=1, V0=1) in a dielectric ball (b=2, eps 4), level {level}: "
+                            f"{len(tri6)} six-node triangles, {nv} vertices, tol 1e-10",
+                  "setup_ms": t_set, **res})
             ctx.close()
     if "c5" in want:
         scale = (200000 / 20068.0) ** 0.5

@@ -431,9 +431,12 @@ void bem_p1_default_params(bem_p1_params* p);
  * first nv of them the triangle corners (vertices, the collocation points); tri6:
  * host int32 [N][6] node indices (corners counter-clockwise about the outward
  * normal, then edge midpoints 01, 12, 20); region: host int32 [N]; regions: host
- * [nregions], conductor or floating kinds only (every vertex's triangles must share
- * its region).  Set-up computes every singular and near-singular integral in FP64 on
- * the device.  Errors: BEM_ERR_ARG, BEM_ERR_DEGENERATE (collinear corners),
+ * [nregions], conductor, floating or dielectric kinds (every vertex's triangles must
+ * share its region).  A dielectric vertex's row is Eq. Final3 with K'u taken as the
+ * mean of the two one-sided normal fields, each the field at x_i +- delta n_i
+ * extrapolated to delta -> 0 from delta and 2 delta (delta = 1e-3 of the mean edge
+ * length at the vertex, n_i the normalised sum of its triangles' normals there).
+ * Set-up computes every singular and near-singular integral in FP64 on the device.  Errors: BEM_ERR_ARG, BEM_ERR_DEGENERATE (collinear corners),
  * BEM_ERR_NOMEM, BEM_ERR_CUDA; on error *out is NULL.
  */
 int bem_p1_create(bem_ctx** out, int64_t nn, const double* nodes, int64_t nv, int64_t N, const int32_t* tri6,

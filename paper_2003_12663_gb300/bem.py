@@ -414,8 +414,8 @@ def _regions(regions):
 class P1Context(Context):
     """Curved six-node triangles with the mapped linear basis, collocation at the
     vertices (bem_p1_create).  nodes [nn, 3] (the first nv the corners), tri6 [N, 6],
-    body [N] region index per triangle, regions as for flat meshes (conductor and
-    floating kinds).  Products, solves, dense rows and fields as Context."""
+    body [N] region index per triangle, regions as for flat meshes (conductor, floating
+    and dielectric kinds).  Products, solves, dense rows and fields as Context."""
 
     def __init__(self, nodes, tri6, nv, body, regions, stream=None, **params):
         import torch

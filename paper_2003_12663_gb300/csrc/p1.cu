@@ -28,8 +28,15 @@
 // Row equations: conductor vertices sum_j v_ij u_j = V0 (Eq. Final1); floating
 // vertices sum_j v_ij u_j - V_f = 0 (Eq. Final2); the neutrality row of a closed
 // floating body in the form Gauss's law gives it, int_body sigma_h dS = 0 (Eq.
-// Final4 with no field inside a conductor).  Dielectric rows and sheets are not
-// built on this path.
+// Final4 with no field inside a conductor); dielectric vertices
+// (eps+ + eps-)/2 u_i + (eps+ - eps-) (K'u)_i = 0 (Eq. Final3), where K'u at a vertex
+// of a C0 mesh of curved triangles is taken through the jump relations (Eq. ADL) as
+// Plemelj's formulas: the mean of the two one-sided normal fields, each the field at
+// x_i +- delta n_i extrapolated to delta -> 0 from delta and 2 delta (delta = 1e-3 of
+// the mean edge at x_i; n_i the normalised sum of the adjacent triangles' normals at
+// that corner).  The regular pairs of those four points go through the far kernel
+// every product; their near pairs' normal fields are computed once at set-up (CSR).
+// Sheets are not built on this path.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -60,7 +67,25 @@ struct P1Data {
     int32_t* phi_all = nullptr;    // [nv] BEM_CONDUCTOR: every row needs phi alone
     double* ones = nullptr;        // [N] density factor of the folded FP64 kernel
     int32_t* d_region = nullptr;   // [N]
+    // dielectric rows (Eq. Final3): K'u at a vertex as the mean of the two one-sided
+    // normal fields, each the field at x_i +- m delta_i n_i (m = 1, 2) extrapolated to
+    // delta -> 0; the four points of dielectric vertex d are 4d .. 4d+3
+    int64_t nd = 0;                // dielectric vertices
+    int32_t* dvert = nullptr;      // [nd] their vertex indices
+    int32_t* didx = nullptr;       // [nv] index of a vertex among them, -1 for other vertices
+    double* dpts = nullptr;        // [4 nd][3] x + delta n, x - delta n, x + 2 delta n, x - 2 delta n
+    double* dnrm = nullptr;        // [nd][3] vertex normal n_i
+    double* dcoef = nullptr;       // [nv][2] (eps+ + eps-)/2 and eps+ - eps- of a dielectric vertex
+    int64_t dnnz = 0;
+    int64_t* dptr = nullptr;       // [4 nd + 1] near pairs of every point, triangles ascending
+    int32_t* dcol = nullptr;       // [dnnz]
+    uint8_t* dflag = nullptr;      // [dnnz] bit0: near in FP32, bit1: in FP64
+    double* dval = nullptr;        // [dnnz][3] c_m (G_k . n_i) of the near-singular integrals
 };
+
+// weight of point k (0..3) of a dielectric vertex in K'u = 2 f(delta) - f(2 delta),
+// f(m delta) the mean of the normal field at x + m delta n and x - m delta n
+__host__ __device__ __forceinline__ double kp_weight(int k) { return k < 2 ? 1.0 : -0.5; }
 
 namespace {
 
@@ -430,6 +455,62 @@ __global__ void k_p1_near_values(P1Data D, const int64_t* __restrict__ ptr, cons
     }
 }
 
+// Dielectric rows: one warp per point of the dielectric vertices (4 per vertex):
+// count (phase 0) or list (phase 1) the triangles near it in the FP32 or the FP64
+// classification.  Triangles ascend.
+__global__ void k_p1_dnear_rows(P1Data D, int phase, const float4* __restrict__ hdr32,
+                                const double4* __restrict__ hdr64, int32_t* __restrict__ count)
+{
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= 4 * D.nd) return;
+    const double* x = D.dpts + 3 * p;
+    const float xf = __double2float_rn(x[0]), yf = __double2float_rn(x[1]), zf = __double2float_rn(x[2]);
+    int64_t pos = phase ? D.dptr[p] : 0;
+    int cnt = 0;
+    for (int64_t T0 = 0; T0 < D.N; T0 += 32) {
+        const int64_t T = T0 + lane;
+        uint8_t f = 0;
+        if (T < D.N) {
+            const bool n32 = !is_far32(xf, yf, zf, hdr32[T]);
+            const bool n64 = !is_far64(x[0], x[1], x[2], hdr64[T]);
+            f = (uint8_t)((n32 ? 1 : 0) | (n64 ? 2 : 0));
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, f != 0);
+        if (phase && f) {
+            const int64_t k = pos + __popc(bal & ((1u << lane) - 1u));
+            D.dcol[k] = (int32_t)T;
+            D.dflag[k] = f;
+        }
+        pos += __popc(bal);
+        cnt += __popc(bal);
+    }
+    if (!phase && lane == 0) count[p] = cnt;
+}
+
+// one warp per near pair of a dielectric vertex's point: the weighted normal field of
+// the three basis functions, kp_weight(k) G_j(x) . n_i
+__global__ void k_p1_dnear_values(P1Data D)
+{
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= D.dnnz) return;
+    int64_t lo = 0, hi = 4 * D.nd - 1;  // the point of entry w
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (D.dptr[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const int64_t p = lo, d = p >> 2;
+    const double x[3] = {D.dpts[3 * p], D.dpts[3 * p + 1], D.dpts[3 * p + 2]};
+    const double* n = D.dnrm + 3 * d;
+    double S[3], G[3][3];
+    p1_pair(D, D.dcol[w], x, -1, true, S, G);
+    if (lane == 0) {
+        const double c = kp_weight((int)(p & 3));
+        for (int k = 0; k < 3; ++k) D.dval[3 * w + k] = c * (G[k][0] * n[0] + G[k][1] * n[1] + G[k][2] * n[2]);
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -462,7 +543,7 @@ __global__ void k_p1_rows(P1Data D, int splits, const double* __restrict__ part,
 {
     const int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (v >= D.nv) return;
+    if (v >= D.nv || D.vkind[v] == BEM_DIELECTRIC) return;  // dielectric rows: k_p1_diel_rows
     double f = 0.0;
     for (int s = lane; s < splits; s += 32) f += part[((int64_t)s * D.nv + v) * 4];
     f *= kInv4Pi;
@@ -476,6 +557,42 @@ __global__ void k_p1_rows(P1Data D, int splits, const double* __restrict__ part,
     if (lane == 0) {
         if (D.vkind[v] == BEM_FLOATING) f -= x[D.nv + D.vaux[v]];
         y[v] = f;
+    }
+}
+
+// Dielectric rows (Eq. Final3), one warp per dielectric vertex i:
+//   y_i = (eps+ + eps-)/2 x_i + (eps+ - eps-) (K'x)_i,
+//   (K'x)_i = sum_k kp_weight(k) E(p_k) . n_i over its four points p_k,
+// E from the regular pairs' partial sums of the points (field components 1..3) and
+// the near pairs' CSR values (those the product's classification left out).
+__global__ void k_p1_diel_rows(P1Data D, int splits, const double* __restrict__ part, uint8_t bit,
+                               const double* __restrict__ x, double* __restrict__ y)
+{
+    const int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (d >= D.nd) return;
+    const int64_t M4 = 4 * D.nd;
+    const double* n = D.dnrm + 3 * d;
+    double f = 0.0;
+    for (int i = lane; i < 4 * splits; i += 32) {
+        const int k = i & 3, sp = i >> 2;
+        const double* q = part + ((int64_t)sp * M4 + 4 * d + k) * 4;
+        f = fma(kp_weight(k), q[1] * n[0] + q[2] * n[1] + q[3] * n[2], f);
+    }
+    f *= kInv4Pi;
+    for (int k = 0; k < 4; ++k) {
+        const int64_t p = 4 * d + k;
+        for (int64_t e = D.dptr[p] + lane; e < D.dptr[p + 1]; e += 32) {
+            if (!(D.dflag[e] & bit)) continue;
+            const int32_t* t6 = D.tri6 + 6 * (int64_t)D.dcol[e];
+            const double* vv = D.dval + 3 * e;
+            f = fma(vv[0], x[t6[0]], fma(vv[1], x[t6[1]], fma(vv[2], x[t6[2]], f)));
+        }
+    }
+    f = warp_sum(f);
+    if (lane == 0) {
+        const int64_t v = D.dvert[d];
+        y[v] = fma(D.dcoef[2 * v], x[v], D.dcoef[2 * v + 1] * f);
     }
 }
 
@@ -515,6 +632,10 @@ __global__ void k_p1_jacobi(P1Data D, int64_t nunk, double* __restrict__ jinv)
         jinv[v] = 1.0;
         return;
     }
+    if (D.vkind[v] == BEM_DIELECTRIC) {  // the jump term (eps+ + eps-)/2
+        jinv[v] = 1.0 / D.dcoef[2 * v];
+        return;
+    }
     double d = 0.0;
     for (int64_t e = D.ptr[v]; e < D.ptr[v + 1]; ++e) {
         if (!(D.flag[e] & 4)) continue;
@@ -543,6 +664,49 @@ __global__ void k_p1_assemble(P1Data D, int64_t row0, int64_t row1, const double
         for (int64_t v = 0; v < D.nv; ++v) row[v] = a[v];
         return;
     }
+    const uint8_t bit = F32 ? 1 : 2;
+    if (D.vkind[r] == BEM_DIELECTRIC) {
+        // (eps+ + eps-)/2 e_r + (eps+ - eps-) K'_r: the normal field of every basis
+        // function at the vertex's four points, weighted
+        const int64_t d = D.didx[r];
+        const double* n = D.dnrm + 3 * d;
+        const double B = D.dcoef[2 * r + 1];
+        for (int k = 0; k < 4; ++k) {
+            const double* p = D.dpts + 3 * (4 * d + k);
+            const float pf[3] = {__double2float_rn(p[0]), __double2float_rn(p[1]), __double2float_rn(p[2])};
+            const double c = kp_weight(k) * B * kInv4Pi;
+            for (int64_t T = 0; T < D.N; ++T) {
+                const bool far = F32 ? is_far32(pf[0], pf[1], pf[2], hdr32[T]) : is_far64(p[0], p[1], p[2], hdr64[T]);
+                if (!far) continue;
+                double s[3] = {0.0, 0.0, 0.0};
+                for (int q = 0; q < D.Q; ++q) {
+                    const double4 nd = node64[T * D.Q + q];
+                    double a;
+                    if (F32) {
+                        const float dx = pf[0] - __double2float_rn(nd.x), dy = pf[1] - __double2float_rn(nd.y),
+                                    dz = pf[2] - __double2float_rn(nd.z);
+                        const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                        const float dn = fmaf(dx, (float)n[0], fmaf(dy, (float)n[1], dz * (float)n[2]));
+                        a = (double)(__double2float_rn(nd.w) * ri * ri * ri * dn);
+                    } else {
+                        const double dx = p[0] - nd.x, dy = p[1] - nd.y, dz = p[2] - nd.z;
+                        const double r2 = dx * dx + dy * dy + dz * dz;
+                        a = nd.w * (dx * n[0] + dy * n[1] + dz * n[2]) / (r2 * sqrt(r2));
+                    }
+                    for (int kk = 0; kk < 3; ++kk) s[kk] = fma(a, D.lam[3 * q + kk], s[kk]);
+                }
+                const int32_t* t6 = D.tri6 + 6 * T;
+                for (int kk = 0; kk < 3; ++kk) row[t6[kk]] += c * s[kk];
+            }
+            for (int64_t e = D.dptr[4 * d + k]; e < D.dptr[4 * d + k + 1]; ++e) {
+                if (!(D.dflag[e] & bit)) continue;
+                const int32_t* t6 = D.tri6 + 6 * (int64_t)D.dcol[e];
+                for (int kk = 0; kk < 3; ++kk) row[t6[kk]] += B * D.dval[3 * e + kk];
+            }
+        }
+        row[r] += D.dcoef[2 * r];
+        return;
+    }
     const double* xv = D.nodes + 3 * r;
     const float xf = __double2float_rn(xv[0]), yf = __double2float_rn(xv[1]), zf = __double2float_rn(xv[2]);
     for (int64_t T = 0; T < D.N; ++T) {
@@ -565,7 +729,6 @@ __global__ void k_p1_assemble(P1Data D, int64_t row0, int64_t row1, const double
         const int32_t* t6 = D.tri6 + 6 * T;
         for (int k = 0; k < 3; ++k) row[t6[k]] += kInv4Pi * s[k];
     }
-    const uint8_t bit = F32 ? 1 : 2;
     for (int64_t e = D.ptr[r]; e < D.ptr[r + 1]; ++e) {
         if (!(D.flag[e] & bit)) continue;
         const int32_t* t6 = D.tri6 + 6 * (int64_t)D.col[e];
@@ -642,7 +805,8 @@ void p1_free(bem_ctx* c)
     P1Data* D = c->p1;
     if (!D) return;
     void* ptrs[] = {D->nodes, D->tri6, D->lam, D->rule, D->sing_rule, D->near_rule, D->near_trule, D->ptr,
-                    D->col, D->flag, D->val, D->neut_w, D->vkind, D->vaux, D->phi_all, D->ones, D->d_region};
+                    D->col, D->flag, D->val, D->neut_w, D->vkind, D->vaux, D->phi_all, D->ones, D->d_region,
+                    D->dvert, D->didx, D->dpts, D->dnrm, D->dcoef, D->dptr, D->dcol, D->dflag, D->dval};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->qnode64) cudaFree(c->qnode64);
@@ -687,6 +851,16 @@ int p1_matvec_impl(bem_ctx* c, int precision, int nrhs, const double* x, double*
         c->cnt.matvecs[precision] += 1;
         k_p1_rows<<<nblk(nv * 32, 128), 128, 0, s>>>(D, splits, c->part, (uint8_t)(f32 ? 1 : 2), xr, n, yr);
         BEM_LAUNCH_CHECK(c);
+        if (D.nd > 0) {
+            // the dielectric vertices' four points: regular pairs' field by the far kernel
+            // (the partial sums of the vertex targets have been read), then the rows
+            const int64_t M4 = 4 * D.nd;
+            const int sp4 = far_splits(c, precision, M4);
+            FarTargets T4{nullptr, nullptr, nullptr, D.dpts, M4};
+            if ((rc = launch_far(c, precision, T4, c->ones, 1, 0, sp4, c->part))) return rc;
+            k_p1_diel_rows<<<nblk(D.nd * 32, 128), 128, 0, s>>>(D, sp4, c->part, (uint8_t)(f32 ? 1 : 2), xr, yr);
+            BEM_LAUNCH_CHECK(c);
+        }
         if (c->nfloat > 0) {
             k_p1_neutral<<<c->nfloat, 256, 0, s>>>(D, xr, yr);
             BEM_LAUNCH_CHECK(c);
@@ -766,6 +940,122 @@ extern "C" void bem_p1_default_params(bem_p1_params* p)
     p->max_refine = 6;
     p->max_points = 131072;
     p->far32_variant = 2;
+}
+
+// Unit normal of the six-node map of triangle t6 at its corner k: dy/dxi x dy/deta of
+// the quadratic Lagrange map there, normalised.
+static void corner_normal(const double* nodes, const int32_t* t6, int k, double* n)
+{
+    const double xi = k == 1 ? 1.0 : 0.0, eta = k == 2 ? 1.0 : 0.0;
+    const double l0 = 1.0 - xi - eta, l1 = xi, l2 = eta;
+    const double Dx[6] = {-(4.0 * l0 - 1.0), 4.0 * l1 - 1.0, 0.0, 4.0 * (l0 - l1), 4.0 * l2, -4.0 * l2};
+    const double De[6] = {-(4.0 * l0 - 1.0), 0.0, 4.0 * l2 - 1.0, -4.0 * l1, 4.0 * l1, 4.0 * (l0 - l2)};
+    double a[3] = {0.0, 0.0, 0.0}, b[3] = {0.0, 0.0, 0.0};
+    for (int m = 0; m < 6; ++m)
+        for (int c = 0; c < 3; ++c) {
+            a[c] += Dx[m] * nodes[3 * (int64_t)t6[m] + c];
+            b[c] += De[m] * nodes[3 * (int64_t)t6[m] + c];
+        }
+    n[0] = a[1] * b[2] - a[2] * b[1];
+    n[1] = a[2] * b[0] - a[0] * b[2];
+    n[2] = a[0] * b[1] - a[1] * b[0];
+    const double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int c = 0; c < 3; ++c) n[c] /= l;
+}
+
+// Dielectric rows: every dielectric vertex's normal (the sum of the unit normals its
+// triangles have at that corner, normalised), its step delta = kDeltaRel times the
+// mean length of the corner-to-corner edges at it, and its four points
+// x +- delta n, x +- 2 delta n; then the near pairs of those points and their FP64
+// near-singular normal fields.
+constexpr double kDeltaRel = 1e-3;
+
+static int p1_dielectric_setup(bem_ctx* c, const double* nodes, const int32_t* tri6,
+                               const std::vector<int32_t>& vkind, const std::vector<int32_t>& vreg)
+{
+    P1Data& D = *c->p1;
+    cudaStream_t s = c->stream;
+    const int64_t nv = D.nv, N = D.N;
+    std::vector<int32_t> dvert, didx(nv, -1);
+    for (int64_t v = 0; v < nv; ++v)
+        if (vkind[v] == BEM_DIELECTRIC) {
+            didx[v] = (int32_t)dvert.size();
+            dvert.push_back((int32_t)v);
+        }
+    D.nd = (int64_t)dvert.size();
+    std::vector<double> coef(2 * nv, 0.0);
+    for (int64_t v = 0; v < nv; ++v)
+        if (vkind[v] == BEM_DIELECTRIC) {
+            const bem_region& R = c->regions[vreg[v]];
+            coef[2 * v] = 0.5 * (R.eps_plus + R.eps_minus);
+            coef[2 * v + 1] = R.eps_plus - R.eps_minus;
+        }
+    int rc;
+    if ((rc = p1_alloc(c, &D.didx, nv)) || (rc = p1_alloc(c, &D.dcoef, 2 * nv))) return rc;
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(D.didx, didx.data(), nv * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(D.dcoef, coef.data(), 2 * nv * 8, cudaMemcpyHostToDevice, s));
+    if (D.nd == 0) return cudaStreamSynchronize(s) == cudaSuccess ? BEM_OK : set_err(c, BEM_ERR_CUDA, "sync");
+    // normals (triangles in order) and mean edge lengths (edges 01 of all triangles,
+    // then 12, then 20)
+    std::vector<double> nrm(3 * nv, 0.0), hsum(nv, 0.0), hcnt(nv, 0.0);
+    for (int64_t T = 0; T < N; ++T)
+        for (int k = 0; k < 3; ++k) {
+            double n[3];
+            corner_normal(nodes, tri6 + 6 * T, k, n);
+            for (int cc = 0; cc < 3; ++cc) nrm[3 * (int64_t)tri6[6 * T + k] + cc] += n[cc];
+        }
+    for (int e = 0; e < 3; ++e)
+        for (int64_t T = 0; T < N; ++T) {
+            const int32_t a = tri6[6 * T + e], b = tri6[6 * T + (e + 1) % 3];
+            double L = 0.0;
+            for (int cc = 0; cc < 3; ++cc) L += (nodes[3 * a + cc] - nodes[3 * b + cc]) * (nodes[3 * a + cc] - nodes[3 * b + cc]);
+            L = std::sqrt(L);
+            hsum[a] += L; hsum[b] += L;
+            hcnt[a] += 1.0; hcnt[b] += 1.0;
+        }
+    std::vector<double> dn(3 * D.nd), dp(12 * D.nd);
+    for (int64_t d = 0; d < D.nd; ++d) {
+        const int64_t v = dvert[d];
+        const double* nv3 = &nrm[3 * v];
+        const double l = std::sqrt(nv3[0] * nv3[0] + nv3[1] * nv3[1] + nv3[2] * nv3[2]);
+        const double delta = kDeltaRel * hsum[v] / hcnt[v];
+        for (int cc = 0; cc < 3; ++cc) dn[3 * d + cc] = nv3[cc] / l;
+        const double m[4] = {1.0, -1.0, 2.0, -2.0};
+        for (int k = 0; k < 4; ++k)
+            for (int cc = 0; cc < 3; ++cc)
+                dp[3 * (4 * d + k) + cc] = nodes[3 * v + cc] + m[k] * delta * dn[3 * d + cc];
+    }
+    const int64_t M4 = 4 * D.nd;
+    int32_t* d_count = nullptr;
+    if ((rc = p1_alloc(c, &D.dvert, D.nd)) || (rc = p1_alloc(c, &D.dnrm, 3 * D.nd)) ||
+        (rc = p1_alloc(c, &D.dpts, 3 * M4)) || (rc = p1_alloc(c, &D.dptr, M4 + 1)) ||
+        (rc = p1_alloc(c, &d_count, M4)))
+        return rc;
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(D.dvert, dvert.data(), D.nd * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(D.dnrm, dn.data(), 3 * D.nd * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(D.dpts, dp.data(), 3 * M4 * 8, cudaMemcpyHostToDevice, s));
+    k_p1_dnear_rows<<<nblk(M4 * 32, 128), 128, 0, s>>>(D, 0, c->hdr32, c->hdr64, d_count);
+    cudaError_t e = cudaGetLastError();
+    std::vector<int32_t> cnt(M4);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_count, M4 * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_count);
+    if (e != cudaSuccess) return set_err(c, BEM_ERR_CUDA, "P1 dielectric near pairs: %s", cudaGetErrorString(e));
+    std::vector<int64_t> ptr(M4 + 1, 0);
+    for (int64_t p = 0; p < M4; ++p) ptr[p + 1] = ptr[p] + cnt[p];
+    D.dnnz = ptr[M4];
+    if ((rc = p1_alloc(c, &D.dcol, D.dnnz)) || (rc = p1_alloc(c, &D.dflag, D.dnnz)) ||
+        (rc = p1_alloc(c, &D.dval, 3 * D.dnnz)))
+        return rc;
+    BEM_CUDA_TRY(c, cudaMemcpyAsync(D.dptr, ptr.data(), (M4 + 1) * 8, cudaMemcpyHostToDevice, s));
+    k_p1_dnear_rows<<<nblk(M4 * 32, 128), 128, 0, s>>>(D, 1, c->hdr32, c->hdr64, nullptr);
+    BEM_LAUNCH_CHECK(c);
+    if (D.dnnz > 0) {
+        k_p1_dnear_values<<<nblk(D.dnnz * 32, 128), 128, 0, s>>>(D);
+        BEM_LAUNCH_CHECK(c);
+    }
+    BEM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    return BEM_OK;
 }
 
 static int p1_create_impl(bem_ctx* c, int64_t nn, const double* nodes, int64_t nv, int64_t N,
@@ -897,6 +1187,7 @@ static int p1_create_impl(bem_ctx* c, int64_t nn, const double* nodes, int64_t n
             c->nnz_prec[BEM_FP64] += (f & 2) ? 1 : 0;
         }
     }
+    if ((rc = p1_dielectric_setup(c, nodes, tri6, vkind, vreg))) return rc;
     // neutrality weights a_f[v] = int_body psi_v dS (per corner, summed in triangle order)
     {
         std::vector<double> nw((size_t)std::max(c->nfloat, 1) * nv, 0.0);
@@ -921,7 +1212,7 @@ static int p1_create_impl(bem_ctx* c, int64_t nn, const double* nodes, int64_t n
     BEM_LAUNCH_CHECK(c);
     size_t need = 0;
     for (int prec = 0; prec < 2; ++prec)
-        for (int64_t M : {nv, (int64_t)c->prm.max_points})
+        for (int64_t M : {nv, (int64_t)c->prm.max_points, 4 * D.nd})
             need = std::max(need, (size_t)far_splits(c, prec, M) * (size_t)M * 4);
     c->part_cap = need;
     c->m = c->prm.gmres_restart;
@@ -977,9 +1268,9 @@ extern "C" int bem_p1_create(bem_ctx** out, int64_t nn, const double* nodes, int
     int nfloat = 0;
     for (int r = 0; r < nregions; ++r) {
         const bem_region& R = regions[r];
-        if (R.kind != BEM_CONDUCTOR && R.kind != BEM_FLOATING)
-            return set_err(nullptr, BEM_ERR_ARG, "bem_p1_create: region %d: only conductor and floating "
-                           "regions are built on the curved-triangle path", r);
+        if (R.kind != BEM_CONDUCTOR && R.kind != BEM_FLOATING && R.kind != BEM_DIELECTRIC)
+            return set_err(nullptr, BEM_ERR_ARG, "bem_p1_create: region %d: only conductor, floating and "
+                           "dielectric regions are built on the curved-triangle path", r);
         if (R.kind == BEM_FLOATING) nfloat = std::max(nfloat, R.floating_id + 1);
     }
     for (int64_t T = 0; T < N; ++T)

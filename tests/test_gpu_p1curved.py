@@ -166,5 +166,66 @@ def test_unsupported_calls(bem):
     with pytest.raises(bem.BemError):
         ctx.matvec(u, precision=bem.DF)
     ctx.close()
-    with pytest.raises(bem.BemError):  # dielectric regions are not built on this path
-        bem.P1Context(nodes, tri6, nv, body, [{"kind": "dielectric", "eps_plus": 1.0, "eps_minus": 4.0}])
+    with pytest.raises(bem.BemError):  # sheets are not built on this path
+        bem.P1Context(nodes, tri6, nv, body, [{"kind": "sheet", "floating_id": 0, "eps_plus": 1.0,
+                                                "eps_minus": 1.0}])
+
+
+# ---------------------------------------------------------------- dielectric rows
+DPARAMS = dict(eta=2.0, g=4, n=24, n_near=(16, 64))  # eta = 2 keeps the oracle's K' rows to ~20 s
+
+
+@pytest.fixture(scope="module")
+def diel(bem, C):
+    """A conductor sphere (a = 1, V0 = 1) inside a dielectric sphere (b = 2, eps 4
+    inside, 1 outside), level 1 each: 42 conductor and 42 dielectric vertices."""
+    nodes, tri6, nv, body = mg.quadratic_bodies([mg.quadratic_sphere(1, 1.0), mg.quadratic_sphere(1, 2.0)])
+    body = np.asarray(body, np.int32)
+    regions = [{"kind": "conductor", "V0": 1.0}, {"kind": "dielectric", "eps_plus": 1.0, "eps_minus": 4.0}]
+    P = C.CurvedProblem(nodes, tri6, nv, **DPARAMS)
+    A, b, vreg = P.system(regions, body)
+    ctx = bem.P1Context(nodes, tri6, nv, body, regions, eta=2.0, far_order=4, sing_order=24,
+                        near_radial=16, near_angular=64)
+    yield (nodes, tri6, nv, body, regions), P, A, b, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 5e-6)], ids=["fp64", "mixed"])
+def test_dielectric_rows_and_products(diel, bem, prec, tol):
+    """Eq. Final3 rows: (eps+ + eps-)/2 u_i + (eps+ - eps-) (K'u)_i with K' the mean of
+    the one-sided normal fields, extrapolated from x_i +- delta n_i and +- 2 delta n_i,
+    the oracle's reading; dense rows and products against the oracle's system."""
+    mesh, P, A, b, ctx = diel
+    nv = mesh[2]
+    G = ctx.assemble_rows(precision=prec).cpu().numpy()
+    assert _rel_rows(G[nv // 2:], A[nv // 2:]) < tol   # the dielectric sphere's rows
+    assert _rel_rows(G, A) < tol
+    x = np.random.default_rng(6).normal(size=(2, ctx.nunk))
+    y = ctx.matvec(torch.tensor(x), precision=prec).cpu().numpy()
+    ref = x @ A.T
+    err = np.abs(y - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    assert err.max() < tol, err
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-6)], ids=["fp64", "mixed"])
+def test_dielectric_solve(diel, bem, C, prec, tol):
+    """The solve against the oracle's LU solution; the charges on the two spheres
+    against Gauss's law within the discretisation error of level 1."""
+    mesh, P, A, b, ctx = diel
+    nodes, tri6, nv, body, regions = mesh
+    u_ref = np.linalg.solve(A, b)
+    assert np.allclose(ctx.rhs().cpu().numpy()[0], b)
+    u, iters, rel = ctx.solve(prec, tol=1e-12)
+    u = u[0].cpu().numpy()
+    assert rel[0] <= 1e-12
+    assert np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) < tol, iters
+    a_, b_, eps, V0 = 1.0, 2.0, 4.0, 1.0
+    Q = 4 * np.pi * V0 / (1.0 / (eps * a_) + (1.0 - 1.0 / eps) / b_)
+    want = np.array([Q / eps, Q * (1.0 - 1.0 / eps)])
+    xi, eta, w = C.duffy(C.CORNERS[0], C.CORNERS[1], C.CORNERS[2], 8)
+    lam = C.linear(xi, eta)
+    q = np.zeros(2)
+    for T in range(len(tri6)):
+        _, J = C.surface(nodes[tri6[T]], xi, eta)
+        q[body[T]] += np.sum(w * J * (lam @ u[tri6[T, :3]]))
+    assert np.all(np.abs(q - want) / want < 0.05), (q, want)
