@@ -21,7 +21,8 @@
 // barriers that every warp reaches once per round (a warp without a line joins
 // the rounds until no warp has one).  On meshes of kSplitMin triangles or more a
 // launch may be made of clusters of up to kCl CTAs: the leader runs the lines, each
-// helper sweeps its own part of the triangles in every round of its leader, and all
+// helper sweeps its own part of the triangles (every ncl-th group of 32, so that the
+// near pairs of a point spread over the cluster) in every round of its leader, and all
 // meet at the hardware cluster barrier twice per round (the round's points pushed
 // into the helpers' shared memory; then the leader reads each helper's partial sums
 // from the helper's shared memory, in rank order).  Every CTA of a cluster runs the
@@ -108,10 +109,10 @@ struct Round {
     double P[kLW][12];
 };
 
-// the triangles [j0, j1) that the cluster's CTA of this rank sweeps in every round:
-// a mesh of kSplitMin triangles or more is split into ncl parts of whole
-// 256-triangle chunks (so every copy of the staging ring stays aligned); a smaller
-// mesh is swept by the leader alone, so its sums do not depend on the cluster size
+// the triangles [j0, j1) that the cluster's CTA of this rank sweeps in every round of
+// the FP64 form: a mesh of kSplitMin triangles or more is split into ncl parts of
+// whole 256-triangle chunks; a smaller mesh is swept by the leader alone, so its sums
+// do not depend on the cluster size
 __device__ __forceinline__ void rank_range(int64_t np, int rank, int ncl, int64_t& j0, int64_t& j1)
 {
     const int parts = np >= kSplitMin ? ncl : 1;
@@ -119,6 +120,31 @@ __device__ __forceinline__ void rank_range(int64_t np, int rank, int ncl, int64_
     j0 = min(np, (int64_t)rank * per);
     j1 = min(np, j0 + per);
 }
+
+// The FP32 form deals the mesh's 32-triangle groups to the cluster's CTAs in turn:
+// group g goes to rank g mod parts (parts = ncl on a mesh of kSplitMin triangles or
+// more, else 1: the leader alone).  Neighbouring triangles, and with them the near
+// pairs of a point (FP64 closed form, the slow part of a round near the surfaces),
+// land on different CTAs, so no CTA keeps the others waiting at the cluster barrier
+// with all of them.  Chunk c of the rank holds its groups c*GW .. c*GW+GW-1 (GW
+// groups per chunk, one per warp); every group starts on a multiple of 32 triangles,
+// so the staging copies stay aligned.
+struct RankGroups {
+    int rank = 0, parts = 1;
+    int64_t ngroups = 0;  // groups of this rank
+    __device__ RankGroups(int64_t np, int r, int ncl)
+    {
+        parts = np >= kSplitMin ? ncl : 1;
+        rank = r;
+        const int64_t G = (np + 31) / 32;
+        ngroups = (r < parts && r < G) ? (G - 1 - r) / parts + 1 : 0;
+    }
+    // first triangle of the rank's k-th group, or -1 past its last
+    __device__ __forceinline__ int64_t first(int64_t k) const
+    {
+        return k < ngroups ? (k * parts + rank) * 32 : -1;
+    }
+};
 
 // cluster size of a tracer launch over meshes of at most np triangles and `lines`
 // lines, on a GPU of num_sms SMs (one tracer CTA per SM): `want` (1..kCl) if given;
@@ -185,29 +211,32 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// issue the copies of the calling warp's triangles of the chunk [c0, c0 + n) into
-// buffer b: thread t of the CTA evaluates triangle c0 + t, so warp w reads only
-// triangles w*32 .. w*32+31 of each chunk, and copies exactly those (coalesced).
+// issue the copies of the calling warp's triangles of the rank's chunk c into buffer
+// b: warp w evaluates group c*GW + w of the rank (lane i its triangle i), and copies
+// exactly those 32 triangles (coalesced) into slots w*32 .. w*32+31.
 // The ring is thus private to each warp: a warp waits for its own copies and
 // synchronises with its own lanes, never with the other warps of the CTA.
 template <int Q>
-__device__ __forceinline__ void stage_chunk(const TArgs& A, Stage32<Q>& S, int b, int64_t c0, int n)
+__device__ __forceinline__ void stage_chunk(const TArgs& A, Stage32<Q>& S, int b, const RankGroups& RG, int64_t c)
 {
-    const int lane = threadIdx.x & 31;
-    const int k0 = (threadIdx.x >> 5) * 32;
-    const int nk = min(n - k0, 32);
-    if (nk <= 0) return;
-    const float4* gn = A.node32 + (c0 + k0) * Q;
+    constexpr int GW = Stage32<Q>::TC / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w >= GW) return;
+    const int64_t j0 = RG.first(c * GW + w);  // this warp's group
+    if (j0 < 0) return;
+    const int nk = (int)min((int64_t)32, A.np - j0);
+    const int k0 = w * 32;
+    const float4* gn = A.node32 + j0 * Q;
     float4* sn = &S.node[b][k0 * Q];
     for (int k = lane; k < nk * Q; k += 32) cp_async16(sn + k, gn + k);
     if (lane < nk) {
-        cp_async16(&S.hdr[b][k0 + lane], A.hdr32 + c0 + k0 + lane);
-        cp_async16(&S.nrm[b][k0 + lane], A.nrm32 + c0 + k0 + lane);
+        cp_async16(&S.hdr[b][k0 + lane], A.hdr32 + j0 + lane);
+        cp_async16(&S.nrm[b][k0 + lane], A.nrm32 + j0 + lane);
     }
-    // u: 16-byte copies of four values (c0 + k0 is a multiple of 32), plain loads for the rest
+    // u: 16-byte copies of four values (j0 is a multiple of 32), plain loads for the rest
     const int n4 = nk / 4;
-    if (lane < n4) cp_async16(&S.u[b][k0 + 4 * lane], A.u32 + c0 + k0 + 4 * lane);
-    if (4 * n4 + lane < nk) S.u[b][k0 + 4 * n4 + lane] = A.u32[c0 + k0 + 4 * n4 + lane];
+    if (lane < n4) cp_async16(&S.u[b][k0 + 4 * lane], A.u32 + j0 + 4 * lane);
+    if (4 * n4 + lane < nk) S.u[b][k0 + 4 * n4 + lane] = A.u32[j0 + 4 * n4 + lane];
 }
 
 // The field at the posted points (slots 0..nt-1: the posting warps in order; NT is
@@ -223,7 +252,7 @@ __device__ __forceinline__ void stage_chunk(const TArgs& A, Stage32<Q>& S, int b
 //  * FP64 form: one plain strided pass per slot, FP64 regular pairs, closed form in
 //    place.
 template <bool F32, int Q, int NT>
-__device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, int64_t j0, int64_t j1)
+__device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, int rank, int ncl)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int tk[NT];
@@ -280,13 +309,15 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, i
             ncnt[s] = 0;
         };
         constexpr int NS = Stage32<Q>::NS;
-        const int64_t nch = (j1 - j0 + TC - 1) / TC;
+        constexpr int GW = TC / 32;
+        const RankGroups RG(A.np, rank, ncl);
+        const int64_t nch = (RG.ngroups + GW - 1) / GW;
         const int t = threadIdx.x;
         // prologue: chunks 0 .. NS-2 in flight (one commit group per chunk, empty past the end);
         // the previous round's reads of the ring ended before the round's entry barrier
 #pragma unroll
         for (int p = 0; p < NS - 1; ++p) {
-            if (p < nch) stage_chunk<Q>(A, S, p, j0 + (int64_t)p * TC, (int)min((int64_t)TC, j1 - j0 - (int64_t)p * TC));
+            if (p < nch) stage_chunk<Q>(A, S, p, RG, p);
             cp_async_commit();
         }
         for (int64_t c = 0; c < nch; ++c) {
@@ -294,10 +325,11 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, i
             cp_async_wait<NS - 2>();  // this lane's copies of chunks 0..c have landed (NS-2 newer groups may be in flight)
             __syncwarp();             // ... for every lane of the warp; and every lane is done with chunk c-1
             const int64_t cn = c + NS - 1;  // its buffer, (c-1) % NS, takes chunk c+NS-1 now
-            if (cn < nch) stage_chunk<Q>(A, S, (int)(cn % NS), j0 + cn * TC, (int)min((int64_t)TC, j1 - j0 - cn * TC));
+            if (cn < nch) stage_chunk<Q>(A, S, (int)(cn % NS), RG, cn);
             cp_async_commit();
-            const int64_t j = j0 + c * TC + t;
-            const bool valid = t < TC && j < j1;
+            const int64_t g0 = warp < GW ? RG.first(c * GW + warp) : -1;
+            const int64_t j = g0 + lane;
+            const bool valid = t < TC && g0 >= 0 && j < A.np;
             bool nearf[NT];
             if (valid) {
                 const float4 nv = S.nrm[b][t];
@@ -360,6 +392,8 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, i
             }
         }
     } else {
+        int64_t j0, j1;
+        rank_range(A.np, rank, ncl, j0, j1);
         for (int s = 0; s < nt; ++s) {
             const int k = (int)__fns(amask, 0, s + 1);
             const double* xs = R.x[k];
@@ -408,10 +442,11 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, i
     }
 }
 
-// This CTA's part of the field at every posted point: the triangles [j0, j1), the
+// This CTA's part of the field at every posted point: the triangles of cluster rank
+// `rank` of ncl (RankGroups in the FP32 form, rank_range in the FP64 form), the
 // variant for the number of posting warps, rounded up to 1, 2, 4 or 8.
 template <bool F32, int Q>
-__device__ __noinline__ void sweep(const TArgs& A, Round& R, int64_t j0, int64_t j1)
+__device__ __noinline__ void sweep(const TArgs& A, Round& R, int rank, int ncl)
 {
     unsigned amask = 0u;
 #pragma unroll
@@ -420,15 +455,15 @@ __device__ __noinline__ void sweep(const TArgs& A, Round& R, int64_t j0, int64_t
     const int nt = __popc(amask);
     if (nt == 0) return;
     if constexpr (!F32) {
-        eval_targets<F32, Q, 1>(A, R, amask, nt, j0, j1);  // the FP64 form loops over the slots
+        eval_targets<F32, Q, 1>(A, R, amask, nt, rank, ncl);  // the FP64 form loops over the slots
     } else if (nt == 1) {
-        eval_targets<F32, Q, 1>(A, R, amask, nt, j0, j1);
+        eval_targets<F32, Q, 1>(A, R, amask, nt, rank, ncl);
     } else if (nt == 2) {
-        eval_targets<F32, Q, 2>(A, R, amask, nt, j0, j1);
+        eval_targets<F32, Q, 2>(A, R, amask, nt, rank, ncl);
     } else if (nt <= 4) {
-        eval_targets<F32, Q, 4>(A, R, amask, nt, j0, j1);
+        eval_targets<F32, Q, 4>(A, R, amask, nt, rank, ncl);
     } else {
-        eval_targets<F32, Q, 8>(A, R, amask, nt, j0, j1);
+        eval_targets<F32, Q, 8>(A, R, amask, nt, rank, ncl);
     }
 }
 
@@ -455,9 +490,7 @@ __device__ void eval_round(const TArgs& A, Round& R)
         }
     }
     cl.sync();
-    int64_t j0, j1;
-    rank_range(A.np, 0, ncl, j0, j1);
-    sweep<F32, Q>(A, R, j0, j1);
+    sweep<F32, Q>(A, R, 0, ncl);
     cl.sync();
 }
 
@@ -486,9 +519,7 @@ __device__ void helper_rounds(Round& R, int rank)
     for (;;) {
         cl.sync();                    // the leader has pushed a round, or the release
         if (R.exit) break;
-        int64_t j0, j1;
-        rank_range(R.args.np, rank, (int)cl.num_blocks(), j0, j1);
-        sweep<F32, Q>(R.args, R, j0, j1);
+        sweep<F32, Q>(R.args, R, rank, (int)cl.num_blocks());
         cta_bar();                    // every warp's partial sums are in R
         for (int i = threadIdx.x; i < kLW * 12; i += kLT) {
             const int k = i / 12, a = (i % 12) / 4, c = i % 4;
