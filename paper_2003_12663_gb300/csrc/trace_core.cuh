@@ -289,6 +289,13 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, i
             zf[s] = __double2float_rn(R.x[tk[s]][2]);
             fx[s] = fy[s] = fz[s] = fi[s] = 0.f;
         }
+        float2 x2[NT / 2 > 0 ? NT / 2 : 1], y2[NT / 2 > 0 ? NT / 2 : 1], z2[NT / 2 > 0 ? NT / 2 : 1];
+#pragma unroll
+        for (int s = 0; s < NT / 2; ++s) {
+            x2[s] = make_float2(xf[2 * s], xf[2 * s + 1]);
+            y2[s] = make_float2(yf[2 * s], yf[2 * s + 1]);
+            z2[s] = make_float2(zf[2 * s], zf[2 * s + 1]);
+        }
         extern __shared__ __align__(16) unsigned char tcore_dyn[];
         Stage32<Q>& S = *reinterpret_cast<Stage32<Q>*>(tcore_dyn);
         constexpr int TC = Stage32<Q>::TC;
@@ -338,17 +345,49 @@ __device__ void eval_targets(const TArgs& A, Round& R, unsigned amask, int nt, i
                 const bool elec = A.electrode[rj] != 0;
                 const float uf = S.u[b][t];
                 float gx[NT], gy[NT], gz[NT];
+                if constexpr (NT >= 2) {
+                    // two points per paired FP32 instruction (the same operations per lane,
+                    // so the sums are those of the scalar loop below, bit for bit)
+                    float2 ax[NT / 2], ay[NT / 2], az[NT / 2];
 #pragma unroll
-                for (int s = 0; s < NT; ++s) gx[s] = gy[s] = gz[s] = 0.f;
+                    for (int s = 0; s < NT / 2; ++s) ax[s] = ay[s] = az[s] = make_float2(0.f, 0.f);
+                    const float2 eps2 = make_float2(1e-20f, 1e-20f);
 #pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const float4 nd = S.node[b][t * Q + q];
+                    for (int q = 0; q < Q; ++q) {
+                        const float4 nd = S.node[b][t * Q + q];
+                        const float2 mx = make_float2(-nd.x, -nd.x), my = make_float2(-nd.y, -nd.y),
+                                     mz = make_float2(-nd.z, -nd.z), w2 = make_float2(nd.w, nd.w);
 #pragma unroll
-                    for (int s = 0; s < NT; ++s) {
-                        const float dx = xf[s] - nd.x, dy = yf[s] - nd.y, dz = zf[s] - nd.z;
-                        const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f))));
-                        const float t3 = nd.w * ri * ri * ri;
-                        gx[s] = fmaf(t3, dx, gx[s]); gy[s] = fmaf(t3, dy, gy[s]); gz[s] = fmaf(t3, dz, gz[s]);
+                        for (int s = 0; s < NT / 2; ++s) {
+                            const float2 dx = __fadd2_rn(x2[s], mx), dy = __fadd2_rn(y2[s], my),
+                                         dz = __fadd2_rn(z2[s], mz);
+                            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+                            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                            const float2 t3 = __fmul2_rn(__fmul2_rn(__fmul2_rn(w2, ri), ri), ri);
+                            ax[s] = __ffma2_rn(t3, dx, ax[s]);
+                            ay[s] = __ffma2_rn(t3, dy, ay[s]);
+                            az[s] = __ffma2_rn(t3, dz, az[s]);
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < NT / 2; ++s) {
+                        gx[2 * s] = ax[s].x; gx[2 * s + 1] = ax[s].y;
+                        gy[2 * s] = ay[s].x; gy[2 * s + 1] = ay[s].y;
+                        gz[2 * s] = az[s].x; gz[2 * s + 1] = az[s].y;
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < NT; ++s) gx[s] = gy[s] = gz[s] = 0.f;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const float4 nd = S.node[b][t * Q + q];
+#pragma unroll
+                        for (int s = 0; s < NT; ++s) {
+                            const float dx = xf[s] - nd.x, dy = yf[s] - nd.y, dz = zf[s] - nd.z;
+                            const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-20f))));
+                            const float t3 = nd.w * ri * ri * ri;
+                            gx[s] = fmaf(t3, dx, gx[s]); gy[s] = fmaf(t3, dy, gy[s]); gz[s] = fmaf(t3, dz, gz[s]);
+                        }
                     }
                 }
 #pragma unroll
