@@ -321,8 +321,11 @@ void bem_default_trace_params(bem_trace_params* tp);
  * int32 [L] (completed steps), xend_dev double [L][3] (end point), any may be NULL.
  * One persistent launch: a CTA of 8 warps traces up to 8 lines, one per warp, whose field
  * evaluations share the CTA's sweeps over the triangles; on meshes of 8,192 triangles
- * or more a cluster of two CTAs shares each sweep (the second CTA takes half of the
- * triangles); precision BEM_FP64 or BEM_MIXED (regular pairs in FP32).
+ * or more a thread-block cluster of up to 8 CTAs (params.trace_cluster, by default
+ * chosen from the mesh size and L) shares each sweep, every CTA taking every
+ * cluster-size-th group of 32 triangles; the sums, grouped by those parts, then agree
+ * between cluster sizes to rounding.  Precision BEM_FP64 or BEM_MIXED (regular pairs
+ * in FP32).
  */
 int bem_trace_lines(bem_ctx* ctx, int32_t precision, const double* u_dev, int64_t L,
                     const double* seeds_dev, const bem_trace_params* tp, double* K_dev,
