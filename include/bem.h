@@ -323,7 +323,8 @@ void bem_default_trace_params(bem_trace_params* tp);
  * evaluations share the CTA's sweeps over the triangles; on meshes of 8,192 triangles
  * or more a thread-block cluster of up to 8 CTAs (params.trace_cluster, by default
  * chosen from the mesh size and L) shares each sweep, every CTA taking every
- * cluster-size-th group of 32 triangles; the sums, grouped by those parts, then agree
+ * cluster-size-th group of 32 triangles (BEM_MIXED; contiguous parts in BEM_FP64);
+ * the sums, grouped by those parts, then agree
  * between cluster sizes to rounding.  Precision BEM_FP64 or BEM_MIXED (regular pairs
  * in FP32).
  */
