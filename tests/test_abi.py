@@ -108,3 +108,44 @@ def test_bad_regions_rejected_before_device(L):
     rc, msg = create({"kind": bem.CONDUCTOR, "V0": 0.0},
                      {"kind": bem.SHEET, "floating_id": 1, "eps_plus": 1.0, "eps_minus": 1.0})
     assert rc == -1 and b"no triangles" in msg
+
+
+STRUCTS = ["bem_region", "bem_mesh", "bem_params", "bem_trace_params", "bem_counters", "bem_tuning",
+           "bem_p1_params", "bem_batch_counters"]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and field
+    offsets (a stale mirror would pass arguments at the wrong offsets)."""
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bem.h"', 'int main(void) {']
+    for name in STRUCTS:
+        cls = getattr(bem, name)
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name in STRUCTS:
+        cls = getattr(bem, name)
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_new_defaults(L):
+    p = bem.default_params()
+    assert p.residual == bem.RESIDUAL_DF_UPDATE      # one double-FP32 residual per solve
+    assert p.trace_cluster == 0 and p.far32_variant == 0
+    assert p.adjoint_checkpoint == 128 and p.adjoint_lines == 256
